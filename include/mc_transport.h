@@ -1,0 +1,234 @@
+/*
+ * mc_transport.h -- C ABI of the GB300 Monte Carlo packet-transport library.
+ *
+ * The library implements the per-iteration Monte Carlo radiative transfer of
+ * Kerzendorf & Sim (2014, "A spectral synthesis code for rapid modelling of
+ * supernovae"), Sect. 2: indivisible energy packets injected at the inner
+ * boundary of homologously expanding spherical shells (Sect. 2.4, Eqs. 9-10),
+ * propagated through Thomson and Sobolev line opacity (Sects. 2.5-2.6,
+ * Eqs. 11-12), with scatter or downbranch line interactions (Sect. 2.5), the
+ * J, nu_bar and J_blue estimators (Sect. 2.7, Eqs. 13, 14, 17), the
+ * radiation-field update (Eqs. 15-16) and the direct-binning spectrum
+ * (Sect. 2.9).  All compute runs in CUDA kernels for sm_103a.
+ *
+ * Conventions common to every entry point:
+ *  - Units are CGS: velocities cm/s, densities cm^-3, times s, frequencies Hz,
+ *    energies erg (level energies in eV where stated).
+ *  - Pointers in descriptors and outputs are HOST pointers unless stated.
+ *    Input arrays are copied to the device during the call; the caller keeps
+ *    ownership.  Output arrays are caller-allocated host buffers.
+ *  - Every function returns mc_status: 0 on success, negative on error
+ *    (MC_ERR_*), positive for warnings (MC_WARN_*).  After an error,
+ *    mc_last_error_message() explains it.  No C++ exception crosses the ABI.
+ *  - A model is used by one host thread at a time; distinct models are
+ *    independent.  Device work is enqueued on the model's CUDA stream.
+ *  - Shell s covers [v_inner[s], v_outer[s]); shells are contiguous and
+ *    ordered outward.  Lines are ordered by strictly DESCENDING frequency, so
+ *    "the next redward line" of Sect. 2.6 is the next index.
+ */
+#ifndef MC_TRANSPORT_H
+#define MC_TRANSPORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mc_status;
+
+#define MC_OK 0
+#define MC_ERR_INVALID_ARG (-1) /* NULL, empty, non-monotone, NaN or negative input */
+#define MC_ERR_OOM (-2)         /* device allocation failed */
+#define MC_ERR_CUDA (-3)        /* a CUDA runtime call failed */
+#define MC_ERR_NOT_READY (-4)   /* run before mc_set_plasma, or read before a run */
+#define MC_ERR_TIMEOUT (-5)     /* the transport kernel hit its deadline */
+#define MC_ERR_UNSUPPORTED (-6) /* option not available for this model */
+#define MC_WARN_CAPPED 1        /* some packets hit max_segments (counted in stats) */
+
+/* Line-interaction modes (Table 1 of the paper). */
+#define MC_LINE_SCATTER 0    /* resonance scattering: re-emit in the absorbing line */
+#define MC_LINE_DOWNBRANCH 1 /* macro atom without internal jumps: re-emit via the
+                                branching table of the activated upper level */
+
+/* Precision modes. */
+#define MC_PRECISION_FP64 0  /* all transport arithmetic in binary64 */
+#define MC_PRECISION_MIXED 1 /* distances and optical depths in binary32; comoving
+                                frequency, line-resonance test and estimators in binary64 */
+
+/* Packet fates reported by mc_read_packets. */
+#define MC_PACKET_ESCAPED 1
+#define MC_PACKET_REABSORBED 2
+#define MC_PACKET_CAPPED 3
+
+/* Per-packet counters reported by mc_read_packets, in this order. */
+#define MC_COUNTER_SEGMENTS 0         /* flight segments (one per event) */
+#define MC_COUNTER_LINE_CHECKS 1      /* line-list entries examined */
+#define MC_COUNTER_RESONANCES 2       /* Sobolev points reached within a segment */
+#define MC_COUNTER_LINE_INTERACTIONS 3
+#define MC_COUNTER_E_SCATTERS 4
+#define MC_COUNTER_SHELL_CROSSINGS 5
+#define MC_N_COUNTERS 6
+
+typedef struct mc_model mc_model; /* opaque; owns all device memory of one model */
+
+/* Model geometry, Sect. 2.1: homologous expansion, r = v t_exp. */
+typedef struct {
+    uint32_t n_shells;      /* S >= 1 */
+    const double *v_inner;  /* [S] cm/s, v_inner[s+1] == v_outer[s] */
+    const double *v_outer;  /* [S] cm/s, > v_inner, < c */
+    const double *n_e;      /* [S] free-electron density, cm^-3, >= 0 */
+    double t_exp;           /* time since explosion, s, > 0 */
+} mc_geometry_desc;
+
+/* Line list, Sects. 2.5-2.6.  f/ion/lower/upper are needed only when the
+ * Sobolev depths are computed by the library (Eq. 12) or in downbranch mode. */
+typedef struct {
+    uint32_t n_lines;       /* L >= 1 */
+    const double *nu;       /* [L] Hz, strictly descending, > 0 */
+    const double *f;        /* [L] absorption oscillator strengths, or NULL */
+    const int32_t *ion;     /* [L] ion index in [0, n_ions), or NULL */
+    const int32_t *lower;   /* [L] lower level in [0, n_levels), or NULL */
+    const int32_t *upper;   /* [L] upper level, > lower, or NULL */
+} mc_line_desc;
+
+/* Atomic data and ion densities for the level populations of Sect. 2.3
+ * (Eqs. 4-5) and the downbranch table.  Level (i, k) is entry i*n_levels + k.
+ * The downbranch table is CSR over upper levels: row r = ion*n_levels + upper
+ * lists, in any fixed order, the lines whose upper level is r (dbr_line) and
+ * the running branching probability (dbr_cdf, non-decreasing, last == 1). */
+typedef struct {
+    uint32_t n_ions, n_levels;
+    const double *energy_ev;   /* [I*K] excitation energy above the ion ground state, eV */
+    const double *g;           /* [I*K] statistical weights, > 0 */
+    const uint8_t *metastable; /* [I*K] 1 = ground/metastable (Eq. 4), 0 = diluted (Eq. 5) */
+    const double *n_ion;       /* [S*I] ion number densities, cm^-3 */
+    const uint32_t *dbr_offset;/* [I*K + 1] or NULL (scatter mode) */
+    const uint32_t *dbr_line;  /* [nnz] line index of each branch */
+    const double *dbr_cdf;     /* [nnz] cumulative branching ratio within the row */
+    int32_t lte_excitation;    /* 1: Eq. 4 for every level; 0: dilute-lte (Eq. 5) */
+} mc_atomic_desc;
+
+/* Run options. */
+typedef struct {
+    int32_t line_mode;          /* MC_LINE_* */
+    int32_t precision;          /* MC_PRECISION_* */
+    int32_t j_blue;             /* 1: accumulate J_blue estimators (Eq. 17) */
+    int32_t record_packets;     /* 1: keep per-packet fates for mc_read_packets */
+    uint32_t spec_bins;         /* spectrum bins, uniform in frequency */
+    double spec_nu_lo, spec_nu_hi; /* spectrum range, Hz */
+    uint64_t max_packets;       /* largest n_packets of any run (sizes packet records) */
+    uint64_t max_segments;      /* per-packet segment cap; 0 = 1e6 */
+    double delta_t;             /* simulated time interval of Eq. 10, s; 0 = 1 s */
+    uint64_t timeout_ns;        /* transport-kernel deadline; 0 = none */
+} mc_run_desc;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns device memory usable on the model's stream, or NULL on failure. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} mc_allocator;
+
+/* Totals of the last run. */
+typedef struct {
+    uint64_t packets, escaped, reabsorbed, capped;
+    uint64_t segments, line_checks, resonances, line_interactions, e_scatters, shell_crossings;
+} mc_packet_stats;
+
+/* Create a model on the current CUDA device.
+ *  geom, lines, run: required.  atomic: required when the library computes the
+ *  Sobolev depths (mc_set_plasma with tau == NULL) or in downbranch mode.
+ *  alloc: NULL = stream-ordered cudaMallocAsync.  stream: a cudaStream_t, or
+ *  NULL for a stream owned by the model.
+ *  Errors: MC_ERR_INVALID_ARG (shape/value checks listed above), MC_ERR_OOM,
+ *  MC_ERR_CUDA.  On error *out is NULL. */
+mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *lines,
+                          const mc_atomic_desc *atomic, const mc_run_desc *run,
+                          const mc_allocator *alloc, void *stream, mc_model **out);
+
+/* Set the plasma state: radiation temperature T_R and dilution factor W of
+ * Eq. 1 per shell, and optionally the Sobolev depths.
+ *  t_rad [S] K or NULL (= 1e4 K, Sect. 2.8); w [S] or NULL (= geometric
+ *  dilution at the shell centre, Sect. 2.8).  tau [S*L] shell-major given
+ *  Sobolev depths, or NULL to recompute them on the device from the
+ *  populations of Eqs. 4-5 and Eq. 12 before the next run (needs atomic data).
+ *  Errors: MC_ERR_INVALID_ARG (NaN/negative values, tau == NULL without
+ *  atomic data). */
+mc_status mc_set_plasma(mc_model *m, const double *t_rad, const double *w, const double *tau);
+
+/* Enqueue one Monte Carlo iteration (Sects. 2.4-2.7, 2.9): recompute the
+ * Sobolev depths if the plasma changed, zero the estimators, inject and
+ * transport n_packets packets from a blackbody of temperature t_inner (K).
+ * Random numbers: Philox4x32-10 (Salmon et al. 2011) with key = seed and
+ * counter (draw block, packet id, iteration, 0), so results depend only on
+ * (seed, iteration, packet id).  Asynchronous on the model's stream.
+ *  Errors: MC_ERR_NOT_READY (no plasma set), MC_ERR_INVALID_ARG
+ *  (n_packets == 0 or > max_packets when records are kept, n_packets >= 2^32,
+ *  t_inner <= 0). */
+mc_status mc_run_iteration(mc_model *m, uint64_t seed, uint32_t iteration, uint64_t n_packets,
+                           double t_inner);
+
+/* Update T_R and W from the last run's estimators (Eqs. 15-16) on the device;
+ * shells with no path length keep their values.  The next run recomputes the
+ * Sobolev depths when they are not given.  Copies the new values to t_rad_out
+ * and w_out ([S], either may be NULL).  Synchronises the stream.
+ *  Errors: MC_ERR_NOT_READY (no run yet), MC_ERR_CUDA. */
+mc_status mc_update_radiation_field(mc_model *m, double *t_rad_out, double *w_out);
+
+/* Read the last run's estimators (synchronises).  Raw sums, any may be NULL:
+ *  j_est[S]   = sum E_cmf l D over segments in the shell, l in units of c t_exp
+ *  nu_bar[S]  = sum E_cmf nu_cmf l D
+ *  j_blue[S*L]= sum E_lab (nu_line/nu_lab)^2 / nu_line over Sobolev points passed
+ *               (shell-major; requires run->j_blue)
+ *  norm[S]    = c t_exp / (4 pi delta_t V): multiplying j_est, nu_bar or j_blue
+ *               by it gives Eqs. 13, 14 and 17 (with the resonance path c t_exp).
+ *  Errors: MC_ERR_NOT_READY, MC_ERR_UNSUPPORTED (j_blue requested but off). */
+mc_status mc_read_estimators(mc_model *m, double *j_est, double *nu_bar, double *j_blue,
+                             double *norm);
+
+/* Read the last run's direct-binning spectrum and totals (synchronises).
+ *  spectrum[spec_bins + 2]: sum of escaping lab energies per bin, then the
+ *  underflow and overflow sums; divide by (delta_t * bin width) for L_nu.
+ *  stats may be NULL.  Returns MC_WARN_CAPPED if any packet was capped. */
+mc_status mc_read_spectrum(mc_model *m, double *spectrum, mc_packet_stats *stats);
+
+/* Read per-packet results [first, first+count) of the last run (requires
+ * record_packets).  Any output may be NULL.  status: MC_PACKET_*; nu, energy:
+ * final lab frequency and energy; counters: [count * MC_N_COUNTERS].
+ *  Errors: MC_ERR_UNSUPPORTED (records off), MC_ERR_INVALID_ARG (range). */
+mc_status mc_read_packets(mc_model *m, uint64_t first, uint64_t count, int32_t *status,
+                          double *nu, double *energy, uint64_t *counters);
+
+/* Read the device-side plasma state: t_rad[S], w[S], tau[S*L] (shell-major,
+ * binary64 even in mixed mode).  Recomputes tau first if it is stale. */
+mc_status mc_read_plasma(mc_model *m, double *t_rad, double *w, double *tau);
+
+/* Device times of the last run, from CUDA events on the model's stream:
+ * ms[0] Sobolev-depth recomputation (0 if none), ms[1] transport,
+ * ms[2] radiation-field update (0 if not run).  Synchronises. */
+mc_status mc_read_timing(mc_model *m, float *ms);
+
+/* Number of kernels this model has launched since creation. */
+mc_status mc_launch_count(const mc_model *m, uint64_t *count);
+
+/* Wait for the model's stream. */
+mc_status mc_synchronize(mc_model *m);
+
+/* Free all device memory of the model (NULL is ignored). */
+void mc_model_destroy(mc_model *m);
+
+/* Static description of a status code. */
+const char *mc_status_string(mc_status s);
+
+/* Message of the model's last error ("" if none); m may be NULL for errors
+ * of mc_model_create. */
+const char *mc_last_error_message(const mc_model *m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MC_TRANSPORT_H */

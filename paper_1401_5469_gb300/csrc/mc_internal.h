@@ -1,0 +1,105 @@
+// Internal declarations of the CUDA library (kernel parameter blocks and
+// launchers).  Not part of the public ABI; see include/mc_transport.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mcgpu {
+
+// Physical constants, CGS (CODATA 2018).
+constexpr double kC = 2.99792458e10;
+constexpr double kH = 6.62607015e-27;
+constexpr double kKB = 1.380649e-16;
+constexpr double kSigmaSB = 5.670374419e-5;
+constexpr double kSigmaT = 6.6524587321e-25;
+constexpr double kMe = 9.1093837015e-28;
+constexpr double kEcharge = 4.803204712570263e-10;
+constexpr double kEv = 1.602176634e-12;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kZeta5 = 1.0369277551433699263;
+
+constexpr int kPlanckLmax = 1024;
+
+// Run-statistics slots (device array of unsigned long long).
+enum Stat : int {
+  kStEscaped = 0, kStReabsorbed, kStCapped, kStSegments, kStLineChecks, kStResonances,
+  kStLineInteractions, kStEScatters, kStShellCrossings, kNStats
+};
+constexpr int kNCounters = 6;
+
+// Everything the transport kernel reads or writes.
+struct TransportParams {
+  int32_t S, L;
+  const double *x_in, *x_out;        // [S] radii in units of c t_exp
+  const double *inv_x_in, *inv_x_out;// [S]
+  const double *kappa;               // [S] sigma_T n_e c t_exp (per unit x)
+  const float *kappa32;              // [S] same, binary32 (mixed mode)
+  const float *x_in32, *x_out32;     // [S] binary32 radii (mixed mode)
+  const double *nu;                  // [L] line frequencies, descending
+  const double *tau;                 // [S*L] Sobolev depths (fp64 mode)
+  const float *tau32;                // [S*L] Sobolev depths (mixed mode)
+  const int32_t *line_row;           // [L] downbranch row of each line
+  const uint32_t *dbr_offset, *dbr_line;
+  const double *dbr_cdf;
+  double *j_est, *nu_bar;            // [S] raw sums
+  double *j_blue;                    // [S*L] raw sums or nullptr
+  double *spectrum;                  // [bins + 2]
+  unsigned long long *stats;         // [kNStats]
+  int32_t spec_bins;
+  double spec_lo, spec_hi, spec_dnu;
+  uint64_t n_packets;
+  uint32_t iteration, key0, key1;
+  double e_cmf;                      // comoving packet energy, Eq. 10
+  double nu_scale;                   // k T_inner / h
+  const double *planck_cdf;          // [kPlanckLmax + 1]
+  uint64_t max_segments;
+  unsigned long long *work_counter;  // next unclaimed packet id
+  int32_t *rec_status;               // per-packet records or nullptrs
+  double *rec_nu, *rec_e;
+  unsigned long long *rec_cnt;       // [n * kNCounters]
+  unsigned long long timeout_ns;     // 0 = none
+  unsigned long long *flags;         // [0]: deadline hit
+};
+
+struct PlasmaParams {
+  int32_t S, I, K, L;
+  const double *t_rad, *w;           // [S]
+  const double *eps_erg, *g;         // [I*K]
+  const uint8_t *metastable;         // [I*K]
+  const double *n_ion;               // [S*I]
+  int32_t lte_excitation;
+  double *pop;                       // [S*I*K]
+  const int32_t *lev_l, *lev_u;      // [L] level index ion*K + level
+  const double *line_pref;           // [L] (pi e^2 / m_e c) f lambda t_exp
+  const double *line_gratio;         // [L] g_l / g_u
+  double *tau;                       // [S*L] or nullptr
+  float *tau32;                      // [S*L] or nullptr
+};
+
+struct UpdateParams {
+  int32_t S;
+  const double *j_est, *nu_bar, *norm;
+  double *t_rad, *w;
+  double c_tr;                       // (h/k) pi^4 / (360 zeta(5))
+};
+
+// Launchers (return the launch error).  `line_mode` 0 scatter / 1 downbranch,
+// `precision` 0 fp64 / 1 mixed.
+cudaError_t launch_transport(const TransportParams &p, int line_mode, int precision, bool j_blue,
+                             bool record, int grid, int block, cudaStream_t st);
+int transport_block_size();
+cudaError_t transport_occupancy(int line_mode, int precision, bool j_blue, bool record,
+                                int *blocks_per_sm);
+cudaError_t launch_populations(const PlasmaParams &p, cudaStream_t st);
+cudaError_t launch_sobolev_tau(const PlasmaParams &p, cudaStream_t st);
+cudaError_t launch_update(const UpdateParams &p, cudaStream_t st);
+cudaError_t launch_zero(double *a, size_t n_a, double *b, size_t n_b, double *c, size_t n_c,
+                        unsigned long long *u, size_t n_u, cudaStream_t st);
+cudaError_t launch_zero_large(double *a, size_t n, cudaStream_t st);
+cudaError_t launch_line_setup(int L, int K, const double *nu, const double *f, const int32_t *ion,
+                              const int32_t *lower, const int32_t *upper, const double *g,
+                              double t_exp, int32_t *lev_l, int32_t *lev_u, double *pref,
+                              double *gratio, int32_t *row, cudaStream_t st);
+
+}  // namespace mcgpu

@@ -1,0 +1,163 @@
+// Plasma-state kernels: level populations (Kerzendorf & Sim 2014, Sect. 2.3,
+// Eqs. 4-5), Sobolev optical depths (Eq. 12), the radiation-field update from
+// the Monte Carlo estimators (Eqs. 15-16) and estimator zeroing.
+#include <cstdint>
+
+#include "mc_internal.h"
+
+namespace mcgpu {
+
+namespace {
+
+// One thread per (shell, ion): partition function over the ion's levels
+// Z = sum_k w_k g_k exp(-eps_k / k T_R) with w_k = 1 for ground/metastable
+// levels (Eq. 4) and w_k = W otherwise (Eq. 5); n_k = w_k g_k N exp(..) / Z.
+__global__ void populations_kernel(const PlasmaParams p) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p.S * p.I) return;
+  const int s = idx / p.I, i = idx - s * p.I;
+  const double inv_kT = 1.0 / (kKB * p.t_rad[s]);
+  const double w = p.w[s];
+  const size_t a0 = static_cast<size_t>(i) * p.K;
+  double Z = 0.0;
+  for (int k = 0; k < p.K; ++k) {
+    const double wk = (p.lte_excitation || p.metastable[a0 + k]) ? 1.0 : w;
+    Z += (wk * p.g[a0 + k]) * exp(-(p.eps_erg[a0 + k] * inv_kT));
+  }
+  const double scale = p.n_ion[static_cast<size_t>(s) * p.I + i] / Z;
+  double *out = p.pop + (static_cast<size_t>(s) * p.I + i) * p.K;
+  for (int k = 0; k < p.K; ++k) {
+    const double wk = (p.lte_excitation || p.metastable[a0 + k]) ? 1.0 : w;
+    out[k] = ((wk * p.g[a0 + k]) * exp(-(p.eps_erg[a0 + k] * inv_kT))) * scale;
+  }
+}
+
+// One thread per line, looping over shells so that each shell row is written
+// with coalesced stores.  Eq. 12 with the stimulated-emission bracket
+// multiplied out: tau = pref (n_l - (g_l/g_u) n_u), pref = (pi e^2/m_e c) f
+// lambda t_exp.  A line whose lower level is empty gets tau = 0.
+__global__ void sobolev_tau_kernel(const PlasmaParams p) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p.L) return;
+  const int ll = __ldg(p.lev_l + j), lu = __ldg(p.lev_u + j);
+  const double pref = __ldg(p.line_pref + j), gr = __ldg(p.line_gratio + j);
+  const size_t IK = static_cast<size_t>(p.I) * p.K;
+  for (int s = 0; s < p.S; ++s) {
+    const double n_l = __ldg(p.pop + s * IK + ll);
+    const double n_u = __ldg(p.pop + s * IK + lu);
+    const double t = (n_l > 0.0) ? pref * fma(-gr, n_u, n_l) : 0.0;
+    const size_t o = static_cast<size_t>(s) * p.L + j;
+    if (p.tau) p.tau[o] = t;
+    if (p.tau32) p.tau32[o] = static_cast<float>(t);
+  }
+}
+
+// Eqs. 15-16; shells without path length keep T_R and W.
+__global__ void update_kernel(const UpdateParams p) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p.S) return;
+  const double j = p.j_est[s];
+  if (!(j > 0.0)) return;
+  const double T = p.c_tr * (p.nu_bar[s] / j);
+  const double J = j * p.norm[s];
+  const double T2 = T * T;
+  p.t_rad[s] = T;
+  p.w[s] = (kPi * J) / (kSigmaSB * (T2 * T2));
+}
+
+__global__ void zero_kernel(double *a, size_t n_a, double *b, size_t n_b, double *c, size_t n_c,
+                            unsigned long long *u, size_t n_u) {
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;; i += stride) {
+    bool any = false;
+    if (i < n_a) { a[i] = 0.0; any = true; }
+    if (i < n_b) { b[i] = 0.0; any = true; }
+    if (i < n_c) { c[i] = 0.0; any = true; }
+    if (i < n_u) { u[i] = 0ull; any = true; }
+    if (!any) break;
+  }
+}
+
+// Wide zeroing with 16-byte stores (n doubles, base 16-byte aligned).
+__global__ void zero_large_kernel(double *a, size_t n) {
+  const size_t n2 = n / 2;
+  double2 *a2 = reinterpret_cast<double2 *>(a);
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n2; i += stride)
+    a2[i] = make_double2(0.0, 0.0);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) a[n - 1] = 0.0;
+}
+
+// Per-line constants of Eq. 12 and the level/branching-row indices.
+__global__ void line_setup_kernel(int L, int K, const double *nu, const double *f,
+                                  const int32_t *ion, const int32_t *lower, const int32_t *upper,
+                                  const double *g, double t_exp, double sob, int32_t *lev_l,
+                                  int32_t *lev_u, double *pref, double *gratio, int32_t *row) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L) return;
+  const int ll = ion[j] * K + lower[j], lu = ion[j] * K + upper[j];
+  lev_l[j] = ll;
+  lev_u[j] = lu;
+  row[j] = lu;
+  if (f) {
+    pref[j] = ((sob * f[j]) * (kC / nu[j])) * t_exp;
+    gratio[j] = g[ll] / g[lu];
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+cudaError_t launch_populations(const PlasmaParams &p, cudaStream_t st) {
+  const int n = p.S * p.I;
+  populations_kernel<<<(n + 127) / 128, 128, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sobolev_tau(const PlasmaParams &p, cudaStream_t st) {
+  sobolev_tau_kernel<<<(p.L + 255) / 256, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const UpdateParams &p, cudaStream_t st) {
+  update_kernel<<<(p.S + 63) / 64, 64, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(double *a, size_t n_a, double *b, size_t n_b, double *c, size_t n_c,
+                        unsigned long long *u, size_t n_u, cudaStream_t st) {
+  size_t n = n_a;
+  if (n_b > n) n = n_b;
+  if (n_c > n) n = n_c;
+  if (n_u > n) n = n_u;
+  const int grid = static_cast<int>((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  zero_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>(a, n_a, b, n_b, c, n_c, u, n_u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_line_setup(int L, int K, const double *nu, const double *f, const int32_t *ion,
+                              const int32_t *lower, const int32_t *upper, const double *g,
+                              double t_exp, int32_t *lev_l, int32_t *lev_u, double *pref,
+                              double *gratio, int32_t *row, cudaStream_t st) {
+  const double sob = ((kPi * kEcharge) * kEcharge) / (kMe * kC);
+  line_setup_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, K, nu, f, ion, lower, upper, g, t_exp, sob,
+                                                     lev_l, lev_u, pref, gratio, row);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_large(double *a, size_t n, cudaStream_t st) {
+  zero_large_kernel<<<sm_count() * 8, 256, 0, st>>>(a, n);
+  return cudaGetLastError();
+}
+
+}  // namespace mcgpu

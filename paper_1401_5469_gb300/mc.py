@@ -1,0 +1,362 @@
+"""Python binding of the C ABI in ``include/mc_transport.h`` (ctypes).
+
+Argument marshalling only: every computation runs in the CUDA library
+``_lib/libmc_gb300.so``.  The functions keep the C names (``mc_model_create``,
+``mc_set_plasma``, ``mc_run_iteration``, ...); ``Model`` wraps them for a
+``synth.ModelSpec``.  PyTorch is used only for the CUDA stream (the model's
+work is enqueued on torch's current stream) and, optionally, for device memory
+through torch's caching allocator.  Importing this module without the built
+library raises ``ImportError``: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+MC_OK = 0
+MC_ERR_INVALID_ARG = -1
+MC_ERR_OOM = -2
+MC_ERR_CUDA = -3
+MC_ERR_NOT_READY = -4
+MC_ERR_TIMEOUT = -5
+MC_ERR_UNSUPPORTED = -6
+MC_WARN_CAPPED = 1
+MC_LINE_SCATTER, MC_LINE_DOWNBRANCH = 0, 1
+MC_PRECISION_FP64, MC_PRECISION_MIXED = 0, 1
+MC_PACKET_ESCAPED, MC_PACKET_REABSORBED, MC_PACKET_CAPPED = 1, 2, 3
+MC_N_COUNTERS = 6
+COUNTER_NAMES = ("segments", "line_checks", "resonances", "line_interactions", "e_scatters",
+                 "shell_crossings")
+
+# Every entry point declared in include/mc_transport.h.
+EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_update_radiation_field",
+            "mc_read_estimators", "mc_read_spectrum", "mc_read_packets", "mc_read_plasma",
+            "mc_read_timing", "mc_launch_count", "mc_synchronize", "mc_model_destroy",
+            "mc_status_string", "mc_last_error_message")
+
+
+class mc_geometry_desc(C.Structure):
+    _fields_ = [("n_shells", C.c_uint32), ("v_inner", C.c_void_p), ("v_outer", C.c_void_p),
+                ("n_e", C.c_void_p), ("t_exp", C.c_double)]
+
+
+class mc_line_desc(C.Structure):
+    _fields_ = [("n_lines", C.c_uint32), ("nu", C.c_void_p), ("f", C.c_void_p),
+                ("ion", C.c_void_p), ("lower", C.c_void_p), ("upper", C.c_void_p)]
+
+
+class mc_atomic_desc(C.Structure):
+    _fields_ = [("n_ions", C.c_uint32), ("n_levels", C.c_uint32), ("energy_ev", C.c_void_p),
+                ("g", C.c_void_p), ("metastable", C.c_void_p), ("n_ion", C.c_void_p),
+                ("dbr_offset", C.c_void_p), ("dbr_line", C.c_void_p), ("dbr_cdf", C.c_void_p),
+                ("lte_excitation", C.c_int32)]
+
+
+class mc_run_desc(C.Structure):
+    _fields_ = [("line_mode", C.c_int32), ("precision", C.c_int32), ("j_blue", C.c_int32),
+                ("record_packets", C.c_int32), ("spec_bins", C.c_uint32),
+                ("spec_nu_lo", C.c_double), ("spec_nu_hi", C.c_double),
+                ("max_packets", C.c_uint64), ("max_segments", C.c_uint64),
+                ("delta_t", C.c_double), ("timeout_ns", C.c_uint64)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class mc_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class mc_packet_stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("packets", "escaped", "reabsorbed", "capped", "segments",
+                                          "line_checks", "resonances", "line_interactions",
+                                          "e_scatters", "shell_crossings")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"CUDA library not built: {_build.LIB}")
+    L = C.CDLL(_build.LIB)
+    vp, i32, u32, u64, d = C.c_void_p, C.c_int32, C.c_uint32, C.c_uint64, C.c_double
+    P = C.POINTER
+    L.mc_model_create.restype = i32
+    L.mc_model_create.argtypes = [P(mc_geometry_desc), P(mc_line_desc), P(mc_atomic_desc),
+                                  P(mc_run_desc), P(mc_allocator), vp, P(vp)]
+    L.mc_set_plasma.restype = i32
+    L.mc_set_plasma.argtypes = [vp, vp, vp, vp]
+    L.mc_run_iteration.restype = i32
+    L.mc_run_iteration.argtypes = [vp, u64, u32, u64, d]
+    L.mc_update_radiation_field.restype = i32
+    L.mc_update_radiation_field.argtypes = [vp, vp, vp]
+    L.mc_read_estimators.restype = i32
+    L.mc_read_estimators.argtypes = [vp, vp, vp, vp, vp]
+    L.mc_read_spectrum.restype = i32
+    L.mc_read_spectrum.argtypes = [vp, vp, P(mc_packet_stats)]
+    L.mc_read_packets.restype = i32
+    L.mc_read_packets.argtypes = [vp, u64, u64, vp, vp, vp, vp]
+    L.mc_read_plasma.restype = i32
+    L.mc_read_plasma.argtypes = [vp, vp, vp, vp]
+    L.mc_read_timing.restype = i32
+    L.mc_read_timing.argtypes = [vp, vp]
+    L.mc_launch_count.restype = i32
+    L.mc_launch_count.argtypes = [vp, P(u64)]
+    L.mc_synchronize.restype = i32
+    L.mc_synchronize.argtypes = [vp]
+    L.mc_model_destroy.restype = None
+    L.mc_model_destroy.argtypes = [vp]
+    L.mc_status_string.restype = C.c_char_p
+    L.mc_status_string.argtypes = [i32]
+    L.mc_last_error_message.restype = C.c_char_p
+    L.mc_last_error_message.argtypes = [vp]
+    _lib = L
+    return L
+
+
+class MCError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _check(code, handle=None, allow_warn=True):
+    if code == MC_OK or (allow_warn and code > 0):
+        return code
+    L = load()
+    msg = L.mc_last_error_message(handle).decode() or L.mc_status_string(code).decode()
+    raise MCError(code, msg)
+
+
+# ----------------------------------------------------------------- raw C names
+
+def mc_model_create(geom, lines, atomic, run, alloc=None, stream=None):
+    L = load()
+    h = C.c_void_p()
+    rc = L.mc_model_create(C.byref(geom), C.byref(lines), C.byref(atomic) if atomic else None,
+                           C.byref(run), C.byref(alloc) if alloc else None, stream, C.byref(h))
+    _check(rc, None)
+    return h
+
+
+def mc_set_plasma(h, t_rad=None, w=None, tau=None):
+    return _check(load().mc_set_plasma(h, _p(t_rad), _p(w), _p(tau)), h)
+
+
+def mc_run_iteration(h, seed, iteration, n_packets, t_inner):
+    return _check(load().mc_run_iteration(h, seed, iteration, n_packets, float(t_inner)), h)
+
+
+def mc_update_radiation_field(h, t_rad_out=None, w_out=None):
+    return _check(load().mc_update_radiation_field(h, _p(t_rad_out), _p(w_out)), h)
+
+
+def mc_read_estimators(h, j_est=None, nu_bar=None, j_blue=None, norm=None):
+    return _check(load().mc_read_estimators(h, _p(j_est), _p(nu_bar), _p(j_blue), _p(norm)), h)
+
+
+def mc_read_spectrum(h, spectrum=None, stats=None):
+    return _check(load().mc_read_spectrum(h, _p(spectrum), C.byref(stats) if stats is not None else None), h)
+
+
+def mc_read_packets(h, first, count, status=None, nu=None, energy=None, counters=None):
+    return _check(load().mc_read_packets(h, first, count, _p(status), _p(nu), _p(energy), _p(counters)), h)
+
+
+def mc_read_plasma(h, t_rad=None, w=None, tau=None):
+    return _check(load().mc_read_plasma(h, _p(t_rad), _p(w), _p(tau)), h)
+
+
+def mc_read_timing(h):
+    ms = np.zeros(3, dtype=np.float32)
+    _check(load().mc_read_timing(h, _p(ms)), h)
+    return ms
+
+
+def mc_launch_count(h):
+    c = C.c_uint64(0)
+    _check(load().mc_launch_count(h, C.byref(c)), h)
+    return int(c.value)
+
+
+def mc_synchronize(h):
+    return _check(load().mc_synchronize(h), h)
+
+
+def mc_model_destroy(h):
+    load().mc_model_destroy(h)
+
+
+# ----------------------------------------------------------------- torch plumbing
+
+def _torch_stream_handle():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class _TorchAllocator:
+    """mc_allocator backed by torch's CUDA caching allocator."""
+
+    def __init__(self, stream_handle):
+        import torch
+        self._torch = torch
+        self._dev = torch.cuda.current_device()
+        self._stream = stream_handle.value
+
+        def _alloc(nbytes, ctx):
+            try:
+                return int(self._torch.cuda.caching_allocator_alloc(nbytes, self._dev, self._stream))
+            except Exception:  # noqa: BLE001 -- report OOM through the C status
+                return None
+
+        def _free(ptr, ctx):
+            self._torch.cuda.caching_allocator_delete(ptr)
+
+        self._a = ALLOC_FN(_alloc)
+        self._f = FREE_FN(_free)
+        self.c = mc_allocator(alloc=self._a, free=self._f, ctx=None)
+
+
+# ----------------------------------------------------------------- Model wrapper
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _u32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.uint32)
+
+
+class Model:
+    """One ejecta model resident on the GPU (wraps a ``synth.ModelSpec``)."""
+
+    def __init__(self, spec, precision: int = MC_PRECISION_FP64, record_packets: bool = False,
+                 max_packets: Optional[int] = None, max_segments: int = 1_000_000,
+                 j_blue: Optional[bool] = None, use_torch_allocator: bool = True,
+                 timeout_ns: int = 0, stream=None):
+        self.spec = spec
+        self._keep = []
+        k = self._keep
+        vi, vo, ne = _f64(spec.v_inner), _f64(spec.v_outer), _f64(spec.n_e)
+        nu = _f64(spec.nu)
+        k += [vi, vo, ne, nu]
+        self.geom = mc_geometry_desc(n_shells=vi.size, v_inner=_p(vi), v_outer=_p(vo), n_e=_p(ne),
+                                     t_exp=float(spec.t_exp))
+        f, ion, lo, up = _f64(spec.f), _i32(spec.ion), _i32(spec.lower), _i32(spec.upper)
+        k += [f, ion, lo, up]
+        self.lines = mc_line_desc(n_lines=nu.size, nu=_p(nu), f=_p(f), ion=_p(ion), lower=_p(lo),
+                                  upper=_p(up))
+        self.atomic = None
+        if spec.energy_ev is not None:
+            e, g = _f64(spec.energy_ev), _f64(spec.g)
+            meta = np.ascontiguousarray(spec.metastable, dtype=np.uint8)
+            nion = _f64(spec.n_ion)
+            off, dl, cdf = _u32(spec.dbr_offset), _u32(spec.dbr_line), _f64(spec.dbr_cdf)
+            k += [e, g, meta, nion, off, dl, cdf]
+            self.atomic = mc_atomic_desc(n_ions=int(spec.n_ions), n_levels=int(spec.n_levels),
+                                         energy_ev=_p(e), g=_p(g), metastable=_p(meta),
+                                         n_ion=_p(nion), dbr_offset=_p(off), dbr_line=_p(dl),
+                                         dbr_cdf=_p(cdf), lte_excitation=0)
+        jb = spec.j_blue if j_blue is None else j_blue
+        mp = int(max_packets if max_packets is not None else spec.n_packets)
+        self.run = mc_run_desc(line_mode=int(spec.line_mode), precision=int(precision),
+                               j_blue=int(bool(jb)), record_packets=int(bool(record_packets)),
+                               spec_bins=int(spec.spec_bins), spec_nu_lo=float(spec.spec_nu_lo),
+                               spec_nu_hi=float(spec.spec_nu_hi), max_packets=mp,
+                               max_segments=int(max_segments), delta_t=1.0,
+                               timeout_ns=int(timeout_ns))
+        self.S, self.L = vi.size, nu.size
+        self.bins = int(spec.spec_bins)
+        self.stream = stream if stream is not None else _torch_stream_handle()
+        self._alloc = _TorchAllocator(self.stream) if use_torch_allocator else None
+        self.h = mc_model_create(self.geom, self.lines, self.atomic, self.run,
+                                 self._alloc.c if self._alloc else None, self.stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            mc_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    # -- plasma and runs
+    def set_plasma(self, t_rad=None, w=None, tau=None):
+        t_rad, w = _f64(t_rad), _f64(w)
+        tau = None if tau is None else _f64(tau).reshape(-1)
+        return mc_set_plasma(self.h, t_rad, w, tau)
+
+    def run_iteration(self, seed, iteration, n_packets, t_inner):
+        return mc_run_iteration(self.h, int(seed), int(iteration), int(n_packets), float(t_inner))
+
+    def update_radiation_field(self):
+        t, w = np.zeros(self.S), np.zeros(self.S)
+        mc_update_radiation_field(self.h, t, w)
+        return t, w
+
+    def estimators(self, j_blue=False):
+        j, nb, norm = np.zeros(self.S), np.zeros(self.S), np.zeros(self.S)
+        jb = np.zeros((self.S, self.L)) if j_blue else None
+        mc_read_estimators(self.h, j, nb, jb, norm)
+        return j, nb, jb, norm
+
+    def spectrum(self):
+        sp = np.zeros(self.bins + 2)
+        st = mc_packet_stats()
+        rc = mc_read_spectrum(self.h, sp, st)
+        return sp, st.as_dict(), rc
+
+    def packets(self, first=0, count=None):
+        if count is None:
+            count = int(self.spectrum()[1]["packets"]) - first
+        status = np.zeros(count, dtype=np.int32)
+        nu, e = np.zeros(count), np.zeros(count)
+        cnt = np.zeros((count, MC_N_COUNTERS), dtype=np.uint64)
+        mc_read_packets(self.h, first, count, status, nu, e, cnt)
+        return status, nu, e, cnt
+
+    def plasma(self):
+        t, w = np.zeros(self.S), np.zeros(self.S)
+        tau = np.zeros((self.S, self.L))
+        mc_read_plasma(self.h, t, w, tau)
+        return t, w, tau
+
+    def timing(self):
+        return mc_read_timing(self.h)
+
+    def launches(self):
+        return mc_launch_count(self.h)
+
+    def synchronize(self):
+        return mc_synchronize(self.h)

@@ -35,7 +35,7 @@ SPEC_NU_HI = 3.0e15   # Hz
 # (T_R = 1e4 K, geometric dilution factor) is e^-2, the median of the
 # lognormal depths of the 2000-line scatter model.  The value is the one
 # printed by oracle/calibrate_ion_density.py for the 500,000-line model.
-ION_DENSITY_SCALE = 1.0e7
+ION_DENSITY_SCALE = 3809298.098545858
 
 
 @dataclasses.dataclass

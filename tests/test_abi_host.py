@@ -1,0 +1,80 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point declared in include/mc_transport.h, and rejects invalid
+models before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1401_5469_gb300 import mc, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "mc_transport.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mc_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = mc.load()
+    names = _declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(mc.EXPORTED) <= set(names)
+
+
+def test_status_strings():
+    L = mc.load()
+    for code in (0, -1, -2, -3, -4, -5, -6, 1):
+        assert L.mc_status_string(code).decode()
+
+
+def _descs(spec, **run_kw):
+    keep = []
+    f64 = lambda a: keep.append(np.ascontiguousarray(a, np.float64)) or keep[-1].ctypes.data
+    g = mc.mc_geometry_desc(n_shells=spec.n_shells, v_inner=f64(spec.v_inner), v_outer=f64(spec.v_outer),
+                            n_e=f64(spec.n_e), t_exp=spec.t_exp)
+    l = mc.mc_line_desc(n_lines=spec.n_lines, nu=f64(spec.nu))
+    r = mc.mc_run_desc(line_mode=0, precision=0, j_blue=0, record_packets=0, spec_bins=10,
+                       spec_nu_lo=1e14, spec_nu_hi=3e15, max_packets=100, max_segments=0, delta_t=1.0)
+    for k, v in run_kw.items():
+        setattr(r, k, v)
+    return g, l, r, keep
+
+
+@pytest.mark.parametrize("mutate,expect", [
+    ("nu_ascending", mc.MC_ERR_INVALID_ARG),
+    ("negative_ne", mc.MC_ERR_INVALID_ARG),
+    ("gap", mc.MC_ERR_INVALID_ARG),
+    ("bad_mode", mc.MC_ERR_INVALID_ARG),
+    ("no_bins", mc.MC_ERR_INVALID_ARG),
+    ("downbranch_without_table", mc.MC_ERR_INVALID_ARG),
+])
+def test_create_rejects_invalid_models(mutate, expect):
+    spec = synth.scatter_model(n_lines=50, n_shells=4)
+    if mutate == "nu_ascending":
+        spec.nu = spec.nu[::-1].copy()
+    elif mutate == "negative_ne":
+        spec.n_e = spec.n_e.copy()
+        spec.n_e[1] = -1.0
+    elif mutate == "gap":
+        spec.v_inner = spec.v_inner.copy()
+        spec.v_inner[2] *= 1.01
+    g, l, r, keep = _descs(spec)
+    if mutate == "bad_mode":
+        r.line_mode = 7
+    elif mutate == "no_bins":
+        r.spec_bins = 0
+    elif mutate == "downbranch_without_table":
+        r.line_mode = 1
+    L = mc.load()
+    h = C.c_void_p()
+    rc = L.mc_model_create(C.byref(g), C.byref(l), None, C.byref(r), None, None, C.byref(h))
+    assert rc == expect
+    assert not h.value
+    assert L.mc_last_error_message(None).decode()
