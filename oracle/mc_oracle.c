@@ -579,9 +579,8 @@ static void spectrum_add(const orc_model *m, double *spec, double nu_lab, double
     if (nu_lab < m->spec_nu_lo) { spec[B] += e_lab; return; }
     double dnu = (m->spec_nu_hi - m->spec_nu_lo) / (double)B;
     double t = (nu_lab - m->spec_nu_lo) / dnu;
-    if (t >= (double)B) { spec[B + 1] += e_lab; return; }
+    if (!(t >= 0.0 && t < (double)B)) { spec[B + 1] += e_lab; return; } /* overflow or NaN */
     int b = (int)floor(t);
-    if (b >= B) { spec[B + 1] += e_lab; return; }
     spec[b] += e_lab;
 }
 

@@ -256,11 +256,13 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       st[kStEScatters] += pk.cnt[4];
       st[kStShellCrossings] += pk.cnt[5];
       if (status == 1) {
+        // bin index; underflow -> bins, overflow (or NaN) -> bins + 1
         int b;
         if (pk.nu_lab < p.spec_lo) b = p.spec_bins;
         else {
           const double t = (pk.nu_lab - p.spec_lo) / p.spec_dnu;
-          b = (t >= static_cast<double>(p.spec_bins)) ? p.spec_bins + 1 : static_cast<int>(floor(t));
+          b = (t >= 0.0 && t < static_cast<double>(p.spec_bins)) ? static_cast<int>(floor(t))
+                                                                   : p.spec_bins + 1;
         }
         atomicAdd(p.spectrum + b, pk.e_lab);
       }
