@@ -1,0 +1,53 @@
+"""Run a synthetic ejecta model for a few Monte Carlo iterations on the GPU.
+
+    python -m paper_1401_5469_gb300.run_model [--model downbranch|scatter]
+        [--lines L] [--packets N] [--iterations K] [--precision fp64|mixed]
+
+Each iteration recomputes the Sobolev depths from T_R and W (downbranch
+model), transports the packets and updates T_R and W (Sect. 2.8).  Prints one
+line of totals and kernel times per iteration.  Used for profiling captures.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+from . import mc, synth
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--model", default="downbranch", choices=["downbranch", "scatter"])
+    ap.add_argument("--lines", type=int, default=None)
+    ap.add_argument("--packets", type=int, default=None)
+    ap.add_argument("--iterations", type=int, default=2)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--seed", type=int, default=5469)
+    a = ap.parse_args()
+    if a.model == "downbranch":
+        kw = {}
+        if a.lines:
+            kw["n_lines"] = a.lines
+        if a.packets:
+            kw["n_packets"] = a.packets
+        spec = synth.downbranch_model(**kw)
+    else:
+        spec = synth.scatter_model(n_lines=a.lines or 2000, n_packets=a.packets or 10_000)
+    prec = mc.MC_PRECISION_FP64 if a.precision == "fp64" else mc.MC_PRECISION_MIXED
+    m = mc.Model(spec, precision=prec)
+    if spec.tau is not None:
+        m.set_plasma(tau=spec.tau)
+    else:
+        m.set_plasma()
+    for it in range(a.iterations):
+        m.run_iteration(a.seed, it, spec.n_packets, spec.t_inner)
+        if spec.tau is None:
+            m.update_radiation_field()
+        _, st, _ = m.spectrum()
+        ms = m.timing()
+        print(json.dumps({"iteration": it, "ms": [float(x) for x in ms], **st}), flush=True)
+    m.close()
+
+
+if __name__ == "__main__":
+    main()
