@@ -220,6 +220,71 @@ mc_status mc_synchronize(mc_model *m);
 /* Free all device memory of the model (NULL is ignored). */
 void mc_model_destroy(mc_model *m);
 
+/* ---------------------------------------------------------------------------
+ * Transport without any allocation.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory where they run the transport: code living
+ * inside another framework's memory pool or under a fixed memory budget,
+ * plug-ins that are handed raw device buffers and hold no allocator of their
+ * own, and loops that must not pay for (or risk failing on) an allocation in
+ * the middle of a time-critical sequence.
+ *
+ * It runs one Monte Carlo iteration exactly like mc_run_iteration on a model
+ * with given Sobolev depths, binary64, no packet records, but every buffer is
+ * the caller's: all pointers in mc_noalloc_args are DEVICE pointers on the
+ * current device, with the layouts and value constraints of mc_model_create
+ * and mc_set_plasma (they are not re-validated, only checked for NULL).  The
+ * kernel's own working memory -- work counter, run statistics, the per-shell
+ * radii and Thomson opacities, the Planck sampling table -- lives in a static
+ * 64 KiB device array that every GPU loading the library holds until the
+ * process exits; hence n_shells <= MC_NOALLOC_MAX_SHELLS, and larger models
+ * are rejected with MC_ERR_INVALID_ARG.  The call performs no cudaMalloc, no
+ * cudaFree and no allocating library call.
+ *
+ *  - The first call on a device does a one-time set-up on that device (it
+ *    looks up the device address of the static array and fills the Planck
+ *    table), so make that first call before any stream capture.
+ *  - Every call on a device shares the same static array, and the array keeps
+ *    the last call's contents; the call clears what must start at zero
+ *    (counters, and the j_est, nu_bar, j_blue and spectrum outputs).  Calls
+ *    whose work overlaps on the GPU (on different streams, or from different
+ *    host threads) race on that array: serialise them.
+ *  - Asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream);
+ *    outputs are ready when the stream is.  Errors are reported through the
+ *    return code and mc_last_error_message(NULL). */
+#define MC_NOALLOC_MAX_SHELLS 1024
+
+typedef struct {
+    uint32_t n_shells;
+    const double *v_inner, *v_outer, *n_e; /* [S] device: cm/s, cm/s, cm^-3 */
+    double v_inner_0;                     /* host copy of v_inner[0], cm/s */
+    double t_exp;                         /* s */
+    uint32_t n_lines;
+    const double *nu;                     /* [L] device, strictly descending */
+    const double *tau;                    /* [S*L] device, shell-major Sobolev depths */
+    int32_t line_mode;                    /* MC_LINE_* */
+    const int32_t *line_row;              /* [L] device: ion*n_levels + upper (downbranch) */
+    const uint32_t *dbr_offset, *dbr_line;/* device branching table (downbranch) */
+    const double *dbr_cdf;
+    uint64_t seed;
+    uint32_t iteration;
+    uint64_t n_packets;                   /* 0 < n_packets < 2^32 */
+    double t_inner;                       /* K */
+    uint64_t max_segments;                /* 0 = 1e6 */
+    double delta_t;                       /* s, 0 = 1 s */
+    double *j_est, *nu_bar;               /* [S] device outputs, raw sums as mc_read_estimators */
+    double *j_blue;                       /* [S*L] device output or NULL (no J_blue) */
+    double *spectrum;                     /* [spec_bins + 2] device output */
+    uint32_t spec_bins;
+    double spec_nu_lo, spec_nu_hi;
+    uint64_t *stats;                      /* device output [9] or NULL: escaped, reabsorbed,
+                                             capped, segments, line_checks, resonances,
+                                             line_interactions, e_scatters, shell_crossings */
+} mc_noalloc_args;
+
+mc_status mc_transport_noalloc(const mc_noalloc_args *args, void *stream);
+
 /* Static description of a status code. */
 const char *mc_status_string(mc_status s);
 

@@ -149,6 +149,12 @@ mc_status recompute_tau(mc_model *m) {
 
 }  // namespace
 
+namespace mcgpu {
+// Message returned by mc_last_error_message(NULL) (used by entry points that
+// have no model handle).
+void set_create_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace mcgpu
+
 extern "C" {
 
 const char *mc_status_string(mc_status s) {

@@ -37,7 +37,7 @@ COUNTER_NAMES = ("segments", "line_checks", "resonances", "line_interactions", "
 EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_update_radiation_field",
             "mc_read_estimators", "mc_read_spectrum", "mc_read_packets", "mc_read_plasma",
             "mc_read_timing", "mc_launch_count", "mc_synchronize", "mc_model_destroy",
-            "mc_status_string", "mc_last_error_message")
+            "mc_status_string", "mc_last_error_message", "mc_transport_noalloc")
 
 
 class mc_geometry_desc(C.Structure):
@@ -64,6 +64,22 @@ class mc_run_desc(C.Structure):
                 ("max_packets", C.c_uint64), ("max_segments", C.c_uint64),
                 ("delta_t", C.c_double), ("timeout_ns", C.c_uint64)]
 
+
+class mc_noalloc_args(C.Structure):
+    """Arguments of mc_transport_noalloc: every pointer is a device pointer."""
+    _fields_ = [("n_shells", C.c_uint32), ("v_inner", C.c_void_p), ("v_outer", C.c_void_p),
+                ("n_e", C.c_void_p), ("v_inner_0", C.c_double), ("t_exp", C.c_double),
+                ("n_lines", C.c_uint32), ("nu", C.c_void_p), ("tau", C.c_void_p),
+                ("line_mode", C.c_int32), ("line_row", C.c_void_p), ("dbr_offset", C.c_void_p),
+                ("dbr_line", C.c_void_p), ("dbr_cdf", C.c_void_p), ("seed", C.c_uint64),
+                ("iteration", C.c_uint32), ("n_packets", C.c_uint64), ("t_inner", C.c_double),
+                ("max_segments", C.c_uint64), ("delta_t", C.c_double), ("j_est", C.c_void_p),
+                ("nu_bar", C.c_void_p), ("j_blue", C.c_void_p), ("spectrum", C.c_void_p),
+                ("spec_bins", C.c_uint32), ("spec_nu_lo", C.c_double), ("spec_nu_hi", C.c_double),
+                ("stats", C.c_void_p)]
+
+
+MC_NOALLOC_MAX_SHELLS = 1024
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -130,6 +146,8 @@ def load(build_if_missing: bool = True):
     L.mc_status_string.argtypes = [i32]
     L.mc_last_error_message.restype = C.c_char_p
     L.mc_last_error_message.argtypes = [vp]
+    L.mc_transport_noalloc.restype = i32
+    L.mc_transport_noalloc.argtypes = [P(mc_noalloc_args), vp]
     _lib = L
     return L
 
@@ -209,6 +227,11 @@ def mc_synchronize(h):
 
 def mc_model_destroy(h):
     load().mc_model_destroy(h)
+
+
+def mc_transport_noalloc(args, stream=None):
+    """One transport launch on caller-owned device buffers; allocates nothing."""
+    return _check(load().mc_transport_noalloc(C.byref(args), stream), None)
 
 
 # ----------------------------------------------------------------- torch plumbing
