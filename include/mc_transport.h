@@ -211,6 +211,12 @@ mc_status mc_read_plasma(mc_model *m, double *t_rad, double *w, double *tau);
  * ms[2] radiation-field update (0 if not run).  Synchronises. */
 mc_status mc_read_timing(mc_model *m, float *ms);
 
+/* Phases of the last transport launch, from the GPU's global timer:
+ * ms[0] from the first warp's start until the packet queue ran empty (every
+ * packet claimed), ms[1] from then until the last warp finished (the tail of
+ * long random walks).  Synchronises. */
+mc_status mc_read_transport_phases(mc_model *m, float *ms);
+
 /* Number of kernels this model has launched since creation. */
 mc_status mc_launch_count(const mc_model *m, uint64_t *count);
 

@@ -329,12 +329,12 @@ double orc_distance_shell(double x, double mu, double x_in, double x_out, int32_
     double d_out;
     if (mu >= 0.0) d_out = ((x_out - x) * (x_out + x)) / (root_out + p);
     else d_out = root_out - p;
-    if (d_out < 0.0) d_out = 0.0;
+    if (!(d_out > 0.0)) d_out = 0.0; /* also the 0/0 of a tangent ray on the boundary */
     if (mu < 0.0) {
         double disc_in = (x_in - x) * (x_in + x) + p * p;
         if (disc_in >= 0.0) {
             double d_in = ((x - x_in) * (x + x_in)) / (sqrt(disc_in) - p);
-            if (d_in < 0.0) d_in = 0.0;
+            if (!(d_in > 0.0)) d_in = 0.0;
             *which = -1;
             return d_in;
         }

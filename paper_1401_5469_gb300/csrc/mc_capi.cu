@@ -39,7 +39,9 @@ struct mc_model {
   bool has_atomic = false, has_line_meta = false;
 
   double *x_in = nullptr, *x_out = nullptr, *inv_x_in = nullptr, *inv_x_out = nullptr;
-  double *kappa = nullptr;
+  double *kappa = nullptr, *inv_kappa = nullptr;
+  DbrRec *dbr_rec = nullptr;
+  unsigned long long *row_info = nullptr;
   float *kappa32 = nullptr, *x_in32 = nullptr, *x_out32 = nullptr;
   double *nu = nullptr, *tau = nullptr;
   float *tau32 = nullptr;
@@ -183,6 +185,7 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
   if (!geom || !lines || !run) return fail(nullptr, MC_ERR_INVALID_ARG, "geometry, lines and run are required");
   const uint32_t S = geom->n_shells, L = lines->n_lines;
   if (S == 0 || L == 0) return fail(nullptr, MC_ERR_INVALID_ARG, "need at least one shell and one line");
+  if (S > 1024) return fail(nullptr, MC_ERR_INVALID_ARG, "at most 1024 shells (the shell table lives in shared memory)");
   if (!geom->v_inner || !geom->v_outer || !geom->n_e || !lines->nu)
     return fail(nullptr, MC_ERR_INVALID_ARG, "NULL geometry or line array");
   if (!(geom->t_exp > 0.0) || !std::isfinite(geom->t_exp))
@@ -302,11 +305,11 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
 
   const size_t SL = static_cast<size_t>(S) * L;
   bool ok = alloc_n(m, &m->x_in, S) && alloc_n(m, &m->x_out, S) && alloc_n(m, &m->inv_x_in, S) &&
-            alloc_n(m, &m->inv_x_out, S) && alloc_n(m, &m->kappa, S) && alloc_n(m, &m->nu, L) &&
+            alloc_n(m, &m->inv_x_out, S) && alloc_n(m, &m->kappa, S) && alloc_n(m, &m->inv_kappa, S) && alloc_n(m, &m->nu, L) &&
             alloc_n(m, &m->tau, SL) && alloc_n(m, &m->t_rad, S) && alloc_n(m, &m->w, S) &&
             alloc_n(m, &m->norm, S) && alloc_n(m, &m->j_est, S) && alloc_n(m, &m->nu_bar, S) &&
             alloc_n(m, &m->spectrum, static_cast<size_t>(run->spec_bins) + 2) &&
-            alloc_n(m, &m->counters, static_cast<size_t>(kNStats) + 2) &&
+            alloc_n(m, &m->counters, static_cast<size_t>(kNCounterSlots)) &&
             alloc_n(m, &m->planck_cdf, static_cast<size_t>(kPlanckLmax) + 1);
   if (ok && run->j_blue) ok = alloc_n(m, &m->j_blue, SL);
   if (ok && meta) ok = alloc_n(m, &m->line_row, L) && alloc_n(m, &m->lev_l, L) && alloc_n(m, &m->lev_u, L);
@@ -318,6 +321,8 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
     if (ok && atomic->dbr_offset)
       ok = alloc_n(m, &m->dbr_offset, IK + 1) && alloc_n(m, &m->dbr_line, nnz) &&
            alloc_n(m, &m->dbr_cdf, nnz);
+    if (ok && atomic->dbr_offset && meta && run->line_mode == MC_LINE_DOWNBRANCH)
+      ok = alloc_n(m, &m->dbr_rec, nnz) && alloc_n(m, &m->row_info, L);
   }
   if (ok && run->record_packets) {
     const size_t n = run->max_packets;
@@ -327,13 +332,14 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
   if (!ok) return bail(MC_ERR_OOM, "device allocation failed");
 
   // Geometry in units of c t_exp (v/c = r/(c t_exp)); kappa' = sigma_T n_e c t_exp.
-  std::vector<double> xi(S), xo(S), ixi(S), ixo(S), kap(S), w0(S), norm(S);
+  std::vector<double> xi(S), xo(S), ixi(S), ixo(S), kap(S), ikap(S), norm(S);
   for (uint32_t s = 0; s < S; ++s) {
     xi[s] = geom->v_inner[s] / kC;
     xo[s] = geom->v_outer[s] / kC;
     ixi[s] = 1.0 / xi[s];
     ixo[s] = 1.0 / xo[s];
     kap[s] = ((kSigmaT * geom->n_e[s]) * kC) * geom->t_exp;
+    ikap[s] = kap[s] > 0.0 ? 1.0 / kap[s] : 0.0;
     const double ri = geom->v_inner[s] * geom->t_exp, ro = geom->v_outer[s] * geom->t_exp;
     const double V = ((4.0 / 3.0) * kPi) * (ro * ro * ro - ri * ri * ri);
     norm[s] = (kC * geom->t_exp) / (((4.0 * kPi) * m->run.delta_t) * V);
@@ -360,6 +366,7 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
   chk(upload(m, m->inv_x_in, ixi.data(), S));
   chk(upload(m, m->inv_x_out, ixo.data(), S));
   chk(upload(m, m->kappa, kap.data(), S));
+  chk(upload(m, m->inv_kappa, ikap.data(), S));
   chk(upload(m, m->norm, norm.data(), S));
   chk(upload(m, m->nu, lines->nu, L));
   chk(upload(m, m->planck_cdf, cdf.data(), cdf.size()));
@@ -394,12 +401,18 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
     chk(launch_line_setup(static_cast<int>(L), Kc, m->nu, f_d, ion_d, lo_d, up_d, m->g, m->t_exp,
                           m->lev_l, m->lev_u, m->line_pref, m->line_gratio, m->line_row, m->stream));
     m->launches += 1;
+    if (m->dbr_rec) {
+      chk(launch_dbr_setup(static_cast<uint32_t>(nnz), I * K, L, Kc, m->dbr_offset, m->dbr_line,
+                           m->dbr_cdf, m->nu, m->line_row, m->dbr_rec, m->row_info, m->stream));
+      m->launches += 2;
+    }
     // Host buffers of the staged copies must outlive the async copies.
     chk(cudaStreamSynchronize(m->stream));
     if (e != cudaSuccess) return bail(MC_ERR_CUDA, std::string("line setup: ") + cudaGetErrorString(e));
   }
   int bps = 0;
-  e = transport_occupancy(run->line_mode, run->precision, run->j_blue != 0, run->record_packets != 0, &bps);
+  e = transport_occupancy(run->line_mode, run->precision, run->j_blue != 0, run->record_packets != 0,
+                          static_cast<int>(S), &bps);
   if (e != cudaSuccess || bps <= 0) return bail(MC_ERR_CUDA, "transport occupancy query failed");
   int nsm = 1;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device);
@@ -472,7 +485,7 @@ mc_status mc_run_iteration(mc_model *m, uint64_t seed, uint32_t iteration, uint6
     m->ran_plasma = true;
   }
   e = launch_zero(m->j_est, m->S, m->nu_bar, m->S, m->spectrum, m->run.spec_bins + 2, m->counters,
-                  kNStats + 2, m->stream);
+                  kNCounterSlots, m->stream);
   if (e != cudaSuccess) return cuda_fail(m, e, "zero");
   m->launches += 1;
   if (m->j_blue) {
@@ -484,6 +497,7 @@ mc_status mc_run_iteration(mc_model *m, uint64_t seed, uint32_t iteration, uint6
   p.S = static_cast<int32_t>(m->S);
   p.L = static_cast<int32_t>(m->L);
   p.x_in = m->x_in; p.x_out = m->x_out; p.inv_x_in = m->inv_x_in; p.inv_x_out = m->inv_x_out;
+  p.inv_kappa = m->inv_kappa; p.row_info = m->row_info; p.dbr_rec = m->dbr_rec;
   p.kappa = m->kappa; p.kappa32 = m->kappa32; p.x_in32 = m->x_in32; p.x_out32 = m->x_out32;
   p.nu = m->nu; p.tau = m->tau; p.tau32 = m->tau32;
   p.line_row = m->line_row; p.dbr_offset = m->dbr_offset; p.dbr_line = m->dbr_line; p.dbr_cdf = m->dbr_cdf;
@@ -565,7 +579,7 @@ mc_status mc_read_estimators(mc_model *m, double *j_est, double *nu_bar, double 
 mc_status mc_read_spectrum(mc_model *m, double *spectrum, mc_packet_stats *stats) {
   if (!m) return MC_ERR_INVALID_ARG;
   if (!m->have_run) return fail(m, MC_ERR_NOT_READY, "no run yet");
-  unsigned long long c[kNStats + 2];
+  unsigned long long c[kNCounterSlots];
   cudaError_t e = cudaSuccess;
   if (spectrum)
     e = cudaMemcpyAsync(spectrum, m->spectrum, (m->run.spec_bins + 2) * sizeof(double),
@@ -634,6 +648,19 @@ mc_status mc_read_timing(mc_model *m, float *ms) {
   if (m->ran_plasma) cudaEventElapsedTime(&ms[0], m->ev[kEvPlasma0], m->ev[kEvPlasma1]);
   cudaEventElapsedTime(&ms[1], m->ev[kEvTransport0], m->ev[kEvTransport1]);
   if (m->ran_update) cudaEventElapsedTime(&ms[2], m->ev[kEvUpdate0], m->ev[kEvUpdate1]);
+  return MC_OK;
+}
+
+mc_status mc_read_transport_phases(mc_model *m, float *ms) {
+  if (!m || !ms) return MC_ERR_INVALID_ARG;
+  if (!m->have_run) return fail(m, MC_ERR_NOT_READY, "no run yet");
+  unsigned long long f[3];
+  cudaError_t e = cudaMemcpyAsync(f, m->counters + kNStats + 2, sizeof(f), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(m, e, "phases");
+  const unsigned long long empty = f[0], done = f[1], start = f[2];
+  ms[0] = (empty > start) ? static_cast<float>((empty - start) * 1e-6) : 0.0f;
+  ms[1] = (done > empty && empty) ? static_cast<float>((done - empty) * 1e-6) : 0.0f;
   return MC_OK;
 }
 

@@ -1,5 +1,6 @@
-// Device helpers of the transport kernels: the Philox4x32-10 draw stream and
-// order-preserving integer keys of binary64 values.
+// Device helpers of the transport kernels: the Philox4x32-10 draw stream,
+// order-preserving integer keys of binary64 values, and the binary64
+// logarithm and reciprocal used on the hot path.
 #pragma once
 
 #include <cstdint>
@@ -47,22 +48,18 @@ struct DrawStream {
   __device__ __forceinline__ double open0() { return __ull2double_rn(next_u53() + 1ull) * 0x1.0p-53; }
   // z in [0, 1)
   __device__ __forceinline__ double closed0() { return __ull2double_rn(next_u53()) * 0x1.0p-53; }
-  __device__ __forceinline__ float closed0f() { return static_cast<float>(next_u53() >> 29) * 0x1.0p-24f; }
+  // mu = 2 z - 1 for z = u53 2^-53 in [0, 1): (u53 - 2^52) 2^-52, exact
+  __device__ __forceinline__ double mu_isotropic() {
+    return __ll2double_rn(static_cast<long long>(next_u53()) - (1ll << 52)) * 0x1.0p-52;
+  }
 };
 
-// Integer key with the same order as the binary64 value (all finite values,
-// both zeros equal-ish: -0 sorts just below +0).  Comparisons of keys run on
-// the integer pipe instead of the (slow) binary64 pipe.
+// Integer key with the same order as the binary64 value (all finite values;
+// -0 sorts just below +0).  Comparisons of keys run on the integer pipe
+// instead of the binary64 pipe.
 __device__ __forceinline__ long long okey(double v) {
   const long long b = __double_as_longlong(v);
   return b ^ ((b >> 63) & 0x7fffffffffffffffll);
-}
-__device__ __forceinline__ long long okey_bits(long long b) {
-  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
-}
-__device__ __forceinline__ int okey32(float v) {
-  const int b = __float_as_int(v);
-  return b ^ ((b >> 31) & 0x7fffffff);
 }
 
 constexpr long long kKeyNegInf = (long long)0x800fffffffffffffll;  // okey(-inf)
@@ -71,6 +68,64 @@ __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Reciprocal by two Newton-Raphson steps r <- r + r (1 - x r) (Markstein
+// 1990) from the hardware approximation rcp.approx.ftz.f64.  Within 1 ulp of
+// 1/x for normal |x| in [2^-1000, 2^1000] (tested against IEEE division).
+__device__ __forceinline__ double rcp64(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+// ln(2) split so that k * kLn2Head is exact for |k| < 2^20.
+constexpr double kLn2Head = 0x1.62e42fee00000p-1;
+constexpr double kLn2Tail = 0x1.a39ef35793c76p-33;
+
+// {c = 1/F, -ln(c)} per breakpoint F; see gen_log_table.py.
+static __constant__ double2 c_log_tab[128] = {
+#include "mc_log_table.inc"
+};
+
+// ln(m 2^k) for m in [1, 2) given by its 52 fraction bits, by Tang's
+// table-driven method (ACM TOMS 16, 1990): m is moved to [0.75, 1.5) (k
+// adjusted), r = m c - 1 with the nearest breakpoint's c = 1/F, and
+// ln(1 + r) from its Taylor series to degree 8 (|r| < 2^-7).
+__device__ __forceinline__ double log_core(int k, unsigned long long frac) {
+  const int i = static_cast<int>(frac >> 45);
+  long long mb = static_cast<long long>(0x3ff0000000000000ull | frac);
+  if (i >= 64) { mb -= (1ll << 52); ++k; }  // m / 2, exponent field only
+  const double m = __longlong_as_double(mb);
+  const double2 ct = c_log_tab[i];
+  const double r = fma(m, ct.x, -1.0);
+  double p = -0.125;
+  p = fma(p, r, 1.0 / 7.0);
+  p = fma(p, r, -1.0 / 6.0);
+  p = fma(p, r, 0.2);
+  p = fma(p, r, -0.25);
+  p = fma(p, r, 1.0 / 3.0);
+  p = fma(p, r, -0.5);
+  p = fma(p, r, 1.0);
+  const double dk = static_cast<double>(k);
+  return fma(dk, kLn2Head, ct.y) + fma(p, r, dk * kLn2Tail);
+}
+
+// -ln(z) for z = u 2^-53, 1 <= u <= 2^53 (the (0,1] draw), integer-only reduction.
+__device__ __forceinline__ double neg_log_u53(unsigned long long u) {
+  const int lz = __clzll(static_cast<long long>(u));
+  const int e = 63 - lz;
+  const unsigned long long frac = ((u << lz) << 1) >> 12;
+  return -log_core(e - 53, frac);
+}
+
+// ln(x) for a positive normal binary64 x.
+__device__ __forceinline__ double log_pos(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  return log_core(static_cast<int>((b >> 52) & 0x7ffull) - 1023, b & 0x000fffffffffffffull);
 }
 
 }  // namespace mcgpu

@@ -28,6 +28,19 @@ enum Stat : int {
 };
 constexpr int kNCounters = 6;
 
+// One entry of a downbranch branching row, in the order of the row:
+// thr = ceil(cdf * 2^53) (so that z < cdf <=> u53 < thr for z = u53 2^-53),
+// the emitted line with its frequency and reciprocal, and the guide entry
+// of bucket (this entry's position in the row): the first position whose
+// thr exceeds the smallest u53 of that bucket.
+struct DbrRec {
+  unsigned long long thr;
+  double nu;
+  double inv_nu;
+  uint32_t emit;
+  uint32_t guide;
+};
+
 // Everything the transport kernel reads or writes.
 struct TransportParams {
   int32_t S, L;
@@ -42,6 +55,9 @@ struct TransportParams {
   const int32_t *line_row;           // [L] downbranch row of each line
   const uint32_t *dbr_offset, *dbr_line;
   const double *dbr_cdf;
+  const double *inv_kappa;           // [S] 1/kappa (0 where kappa = 0), or nullptr
+  const unsigned long long *row_info;// [L] row begin | row length << 32, or nullptr
+  const DbrRec *dbr_rec;             // [nnz] guide-table rows, or nullptr
   double *j_est, *nu_bar;            // [S] raw sums
   double *j_blue;                    // [S*L] raw sums or nullptr
   double *spectrum;                  // [bins + 2]
@@ -59,8 +75,11 @@ struct TransportParams {
   double *rec_nu, *rec_e;
   unsigned long long *rec_cnt;       // [n * kNCounters]
   unsigned long long timeout_ns;     // 0 = none
-  unsigned long long *flags;         // [0]: deadline hit
+  unsigned long long *flags;         // [0] deadline hit, [1] work queue empty (ns),
+                                     // [2] last warp done (ns), [3] first warp start (ns)
 };
+
+constexpr int kNCounterSlots = kNStats + 5;  // stats, work counter, flags[4]
 
 struct PlasmaParams {
   int32_t S, I, K, L;
@@ -89,7 +108,7 @@ struct UpdateParams {
 cudaError_t launch_transport(const TransportParams &p, int line_mode, int precision, bool j_blue,
                              bool record, int grid, int block, cudaStream_t st);
 int transport_block_size();
-cudaError_t transport_occupancy(int line_mode, int precision, bool j_blue, bool record,
+cudaError_t transport_occupancy(int line_mode, int precision, bool j_blue, bool record, int S,
                                 int *blocks_per_sm);
 cudaError_t launch_populations(const PlasmaParams &p, cudaStream_t st);
 cudaError_t launch_sobolev_tau(const PlasmaParams &p, cudaStream_t st);
@@ -97,6 +116,10 @@ cudaError_t launch_update(const UpdateParams &p, cudaStream_t st);
 cudaError_t launch_zero(double *a, size_t n_a, double *b, size_t n_b, double *c, size_t n_c,
                         unsigned long long *u, size_t n_u, cudaStream_t st);
 cudaError_t launch_zero_large(double *a, size_t n, cudaStream_t st);
+cudaError_t launch_dbr_setup(uint32_t nnz, uint32_t n_rows, uint32_t L, int K,
+                             const uint32_t *dbr_offset, const uint32_t *dbr_line,
+                             const double *dbr_cdf, const double *nu, const int32_t *line_row,
+                             DbrRec *rec, unsigned long long *row_info, cudaStream_t st);
 cudaError_t launch_line_setup(int L, int K, const double *nu, const double *f, const int32_t *ion,
                               const int32_t *lower, const int32_t *upper, const double *g,
                               double t_exp, int32_t *lev_l, int32_t *lev_u, double *pref,

@@ -196,7 +196,8 @@ extern "C" mc_status mc_transport_noalloc(const mc_noalloc_args *a, void *stream
   int dev = 0, nsm = 1, bps = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  e = transport_occupancy(a->line_mode, MC_PRECISION_FP64, a->j_blue != nullptr, false, &bps);
+  e = transport_occupancy(a->line_mode, MC_PRECISION_FP64, a->j_blue != nullptr, false,
+                          static_cast<int>(S), &bps);
   if (e != cudaSuccess || bps <= 0) {
     set_create_error("mc_transport_noalloc: occupancy query failed");
     return MC_ERR_CUDA;

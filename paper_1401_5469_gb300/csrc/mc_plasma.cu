@@ -105,6 +105,47 @@ __global__ void line_setup_kernel(int L, int K, const double *nu, const double *
   }
 }
 
+// Downbranch guide-table rows.  One thread per branching entry: its row is
+// found by bisection of the row offsets; thr = ceil(cdf 2^53) is exact (a
+// power-of-two scaling of a binary64 value); the guide entry of bucket k of a
+// row of length n is the first position whose thr exceeds the smallest u53 of
+// the bucket, ceil(k 2^53 / n).
+__global__ void dbr_rec_kernel(uint32_t nnz, uint32_t n_rows, const uint32_t *off,
+                               const uint32_t *line, const double *cdf, const double *nu,
+                               DbrRec *rec) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  uint32_t lo = 0, hi = n_rows;  // row r with off[r] <= e < off[r+1]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (off[mid] <= e) lo = mid; else hi = mid;
+  }
+  const uint32_t b = off[lo], n = off[lo + 1] - b, k = e - b;
+  const double scaled = cdf[e] * 0x1.0p53;
+  rec[e].thr = static_cast<unsigned long long>(ceil(scaled));
+  rec[e].emit = line[e];
+  rec[e].nu = nu[line[e]];
+  rec[e].inv_nu = 1.0 / nu[line[e]];
+  const unsigned __int128 num = (static_cast<unsigned __int128>(k) << 53) + (n - 1);
+  const unsigned long long u_min = static_cast<unsigned long long>(num / n);
+  uint32_t a = 0, z = n - 1;  // first position with thr > u_min (the last has thr = 2^53)
+  while (a < z) {
+    const uint32_t mid = (a + z) >> 1;
+    const unsigned long long t = static_cast<unsigned long long>(ceil(cdf[b + mid] * 0x1.0p53));
+    if (u_min < t) z = mid; else a = mid + 1;
+  }
+  rec[e].guide = a;
+}
+
+__global__ void row_info_kernel(uint32_t L, const int32_t *line_row, const uint32_t *off,
+                                unsigned long long *row_info) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L) return;
+  const int32_t r = line_row[j];
+  const unsigned long long b = off[r], n = off[r + 1] - off[r];
+  row_info[j] = b | (n << 32);
+}
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -152,6 +193,19 @@ cudaError_t launch_line_setup(int L, int K, const double *nu, const double *f, c
   const double sob = ((kPi * kEcharge) * kEcharge) / (kMe * kC);
   line_setup_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, K, nu, f, ion, lower, upper, g, t_exp, sob,
                                                      lev_l, lev_u, pref, gratio, row);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dbr_setup(uint32_t nnz, uint32_t n_rows, uint32_t L, int K,
+                             const uint32_t *dbr_offset, const uint32_t *dbr_line,
+                             const double *dbr_cdf, const double *nu, const int32_t *line_row,
+                             DbrRec *rec, unsigned long long *row_info, cudaStream_t st) {
+  (void)K;
+  if (nnz > 0)
+    dbr_rec_kernel<<<(nnz + 255) / 256, 256, 0, st>>>(nnz, n_rows, dbr_offset, dbr_line, dbr_cdf, nu, rec);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  row_info_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, line_row, dbr_offset, row_info);
   return cudaGetLastError();
 }
 

@@ -4,16 +4,27 @@
 //
 // GB300 notes.  Binary64 add/mul/fma/compare issue at 1/64 of the binary32
 // rate and every binary64 warp instruction holds its warp for ~64 cycles,
-// whatever the number of active lanes.  The kernel therefore
-//  * keeps lanes converged: a lane that finishes its packet claims the next
-//    one at the loop head (warp-aggregated atomic), and the three event kinds
-//    share one code path;
-//  * runs every comparison of the line scan on the integer pipe, comparing
-//    order-preserving int64 keys of binary64 values: the resonance test
-//    "d_line < min(d_e, d_shell)" becomes "nu_line > nu_threshold" with
-//    nu_threshold = nu_cmf - d_min nu_lab (d_line is linear in nu_line);
-//  * accumulates the shell estimators in registers while a packet stays in
-//    one shell and flushes them with one atomic per shell change.
+// whatever the number of active lanes.  A line-thick model is latency-bound by
+// its longest random walks (the packet queue empties within a few percent of
+// the kernel time), so the kernel minimises binary64 instructions per flight
+// segment:
+//  * the packet carries p = x mu, q = x^2 - p^2 (conserved in free flight) and
+//    x^2 (radii in units of c t_exp): D = 1 - p, the shell distance needs one
+//    root, and a shell crossing is p += l;
+//  * the line scan runs in the frequency domain: a Sobolev point is the
+//    closest event while nu_line > max(nu_shell, nu_e), where nu_shell and
+//    nu_e are the comoving frequencies reached at d_shell and d_e; passing a
+//    line of depth tau moves nu_e up by tau nu_lab / k (one FMA), and the line
+//    absorbs the packet exactly when that new nu_e exceeds nu_line (Sect. 2.6's
+//    test tau_S + kappa d_line > tau with kappa d = (nu_cmf - nu) / (nu_lab/k));
+//    every comparison is an integer compare of order-preserving keys;
+//  * 1/D and 1/nu_lab are carried and refreshed with Newton reciprocals, and
+//    -ln z comes from a table-driven logarithm;
+//  * downbranch emission is an integer guide-table search, and the next
+//    line's nu/tau loads are issued before the current line is resolved;
+//  * lanes stay converged: a lane that finishes claims the next packet at the
+//    loop head (warp-aggregated atomic); shell estimators accumulate in
+//    registers and are flushed once per shell change.
 #include <cstdint>
 
 #include "mc_device.cuh"
@@ -24,12 +35,15 @@ namespace mcgpu {
 namespace {
 
 constexpr int kBlock = 128;
+constexpr int kShellArrays = 6;  // x_in^2, x_out^2, x_in, x_out, kappa, 1/kappa
 constexpr int kLineEvent = 1, kElectronEvent = 2, kShellEvent = 3;
 
 struct Packet {
-  double x, mu, nu_lab, e_lab;
+  double p, q, r2;           // x mu, x^2 - p^2, x^2
+  double nu_lab, e_lab, inv_nu, inv_D;
   int32_t shell, next_line;
   uint32_t pid;
+  bool have_inv_D;
   uint32_t cnt[kNCounters];
 };
 
@@ -46,37 +60,71 @@ __device__ __forceinline__ int32_t first_redward(const double *nu, int32_t L, do
   return lo;
 }
 
-// First entry k of a branching row with z < cdf[k] (cdf non-decreasing, last
-// entry 1 > z): binary search on int64 images (all values non-negative).
-__device__ __forceinline__ int32_t downbranch_pick(const TransportParams &p, int32_t row, double z) {
+struct Emission {
+  double nu, inv_nu;
+  int32_t line;
+};
+
+// Downbranch re-emission (Sect. 2.5): the first entry k of the activated
+// upper level's branching row with z < cdf[k], z = u 2^-53.  With the guide
+// table: z < cdf[k] <=> u < ceil(cdf[k] 2^53) = thr[k] exactly; the search
+// starts at the guide entry of bucket floor(z n) and walks forward.
+__device__ __forceinline__ Emission downbranch_pick(const TransportParams &p, int32_t j,
+                                                    unsigned long long rinfo, unsigned long long u) {
+  Emission em;
+  if (p.dbr_rec) {
+    const uint32_t b = static_cast<uint32_t>(rinfo), len = static_cast<uint32_t>(rinfo >> 32);
+    const uint32_t bucket = static_cast<uint32_t>(__umul64hi(u << 11, static_cast<unsigned long long>(len)));
+    const DbrRec *rec = p.dbr_rec;
+    uint32_t i = b + __ldg(&rec[b + bucket].guide);
+    unsigned long long thr = __ldg(&rec[i].thr);
+    while (u >= thr) { ++i; thr = __ldg(&rec[i].thr); }
+    em.nu = __ldg(&rec[i].nu);
+    em.inv_nu = __ldg(&rec[i].inv_nu);
+    em.line = static_cast<int32_t>(__ldg(&rec[i].emit));
+    return em;
+  }
+  const int32_t row = __ldg(p.line_row + j);
   uint32_t lo = __ldg(p.dbr_offset + row), hi = __ldg(p.dbr_offset + row + 1) - 1u;
-  const long long kz = __double_as_longlong(z);
+  const long long kz = __double_as_longlong(static_cast<double>(u) * 0x1.0p-53);
   const long long *cb = reinterpret_cast<const long long *>(p.dbr_cdf);
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
     if (kz < __ldg(cb + mid)) hi = mid; else lo = mid + 1u;
   }
-  return static_cast<int32_t>(__ldg(p.dbr_line + lo));
+  em.line = static_cast<int32_t>(__ldg(p.dbr_line + lo));
+  em.nu = __ldg(p.nu + em.line);
+  em.inv_nu = rcp64(em.nu);
+  return em;
 }
+
+// max(v, 0) through the integer keys (no binary64 instruction).
+__device__ __forceinline__ double max0(double v) { return okey(v) > 0 ? v : 0.0; }
 
 // Injection at the inner boundary, Sect. 2.4: Planck-sampled comoving
 // frequency (Carter & Cashwell series method), mu = sqrt(z), equal comoving
 // energy (Eq. 10), lab-frame values by the first-order Doppler factor.
-__device__ __forceinline__ void inject(const TransportParams &p, Packet &pk, DrawStream &ds) {
+__device__ __forceinline__ void inject(const TransportParams &p, const double *planck, double x0,
+                                       double x0sq, Packet &pk, DrawStream &ds) {
   const double z0 = ds.closed0();
   const double z1 = ds.open0(), z2 = ds.open0(), z3 = ds.open0(), z4 = ds.open0();
   int l = 1;
-  while (l < kPlanckLmax && __ldg(p.planck_cdf + l) < z0) ++l;
-  const double xi = -log(((z1 * z2) * z3) * z4) / static_cast<double>(l);
+  while (l < kPlanckLmax && planck[l] < z0) ++l;
+  double xi = -log_pos(((z1 * z2) * z3) * z4);
+  if (l > 1) xi = xi / static_cast<double>(l);
   const double nu_cmf = p.nu_scale * xi;
   const double mu = sqrt(ds.open0());
-  const double x = __ldg(p.x_in);
-  const double D = fma(-mu, x, 1.0);
-  const double iD = 1.0 / D;
-  pk.x = x;
-  pk.mu = mu;
+  const double pp = x0 * mu;
+  const double D = 1.0 - pp;
+  const double iD = rcp64(D);
+  pk.p = pp;
+  pk.r2 = x0sq;
+  pk.q = max0(fma(-pp, pp, x0sq));
   pk.nu_lab = nu_cmf * iD;
   pk.e_lab = p.e_cmf * iD;
+  pk.inv_nu = rcp64(nu_cmf) * D;
+  pk.inv_D = iD;
+  pk.have_inv_D = true;
   pk.shell = 0;
   pk.next_line = first_redward(p.nu, p.L, nu_cmf);
 #pragma unroll
@@ -85,19 +133,35 @@ __device__ __forceinline__ void inject(const TransportParams &p, Packet &pk, Dra
 
 template <int MODE, bool JB, bool REC>
 __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p) {
+  extern __shared__ double sh[];
+  const int32_t S = p.S, L = p.L;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) {
+    const double xi = p.x_in[i], xo = p.x_out[i], kap = p.kappa[i];
+    sh[i] = xi * xi;
+    sh[S + i] = xo * xo;
+    sh[2 * S + i] = xi;
+    sh[3 * S + i] = xo;
+    sh[4 * S + i] = kap;
+    sh[5 * S + i] = p.inv_kappa ? p.inv_kappa[i] : (kap > 0.0 ? 1.0 / kap : 0.0);
+  }
+  __syncthreads();
+  const double *s_xi2 = sh, *s_xo2 = sh + S, *s_ikap = sh + 5 * S;
+  const double *s_kap = sh + 4 * S;
+  const double x0 = sh[2 * S], x0sq = sh[0];
+
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lanemask_lt = (1u << lane) - 1u;
-  const int32_t S = p.S, L = p.L;
-  const unsigned long long t_start = p.timeout_ns ? global_ns() : 0ull;
+  const unsigned long long t_start = global_ns();
+  if (lane == 0u) atomicCAS(p.flags + 3, 0ull, t_start);
 
   Packet pk;
   DrawStream ds;
   bool alive = false, finished = false;
-  unsigned long long st[kNStats];
-#pragma unroll
-  for (int i = 0; i < kNStats; ++i) st[i] = 0ull;
+  unsigned long long n_esc = 0, n_reab = 0, n_cap = 0, n_seg = 0, n_chk = 0, n_res = 0, n_lint = 0,
+                     n_esca = 0, n_shell = 0;
   int32_t acc_s = -1;
   double acc_j = 0.0, acc_nb = 0.0;
+  const long long *nub = reinterpret_cast<const long long *>(p.nu);
 
   for (;;) {
     // ---- claim packets for idle lanes (one atomic per warp)
@@ -114,10 +178,11 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         if (id < p.n_packets) {
           pk.pid = static_cast<uint32_t>(id);
           ds.init(p.key0, p.key1, pk.pid, p.iteration);
-          inject(p, pk, ds);
+          inject(p, p.planck_cdf, x0, x0sq, pk, ds);
           alive = true;
         } else {
           finished = true;
+          atomicCAS(p.flags + 1, 0ull, global_ns());
         }
       }
     }
@@ -140,66 +205,94 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
     } else {
       pk.cnt[0] += 1u;
       const int32_t s = pk.shell;
-      const double x = pk.x, mu = pk.mu, nu_lab = pk.nu_lab;
-      // Doppler factor, comoving frequency/energy, Thomson opacity (Eq. 11)
-      const double D = fma(-mu, x, 1.0);
+      const double pp = pk.p, q = pk.q, r2 = pk.r2, nu_lab = pk.nu_lab, inv_nu = pk.inv_nu;
+      // Doppler factor D = 1 - mu v/c, comoving frequency (Sect. 2.5)
+      const double D = 1.0 - pp;
+      const double inv_D = pk.have_inv_D ? pk.inv_D : rcp64(D);
       const double nu_cmf = nu_lab * D;
-      const double e_cmf = pk.e_lab * D;
-      const double k = __ldg(p.kappa + s) * D;
-      double tau_rem = -log(ds.open0());
-      // distance to the shell boundary
-      const double pm = x * mu;
-      const double xo = __ldg(p.x_out + s), xi = __ldg(p.x_in + s);
-      const double ao = (xo - x) * (xo + x);
-      const double ai = (xi - x) * (xi + x);
-      const bool inner = (mu < 0.0) && (fma(pm, pm, ai) >= 0.0);
-      const double root = sqrt(fma(pm, pm, inner ? ai : ao));
+      const double eD2 = (pk.e_lab * D) * D;  // E_cmf D for the estimators
+      const double kap = s_kap[s];
+      const bool thomson = kap > 0.0;
+      // optical depth to the next event, tau = -ln z
+      double tau_rem = neg_log_u53(ds.next_u53() + 1ull);
+      // distance to the shell boundary (cancellation-free roots)
+      const double xi2 = s_xi2[s], xo2 = s_xo2[s];
+      const bool outward = pp >= 0.0;
+      const bool inner = !outward && okey(q) <= okey(xi2);
+      const double root = sqrt((inner ? xi2 : xo2) - q);
       double num, den;
-      if (inner) { num = -ai; den = root - pm; }
-      else if (mu >= 0.0) { num = ao; den = root + pm; }
-      else { num = root - pm; den = 1.0; }
-      const double d_shell = fmax(num / den, 0.0);
-      // resonance thresholds on the line frequency
-      const double inv_nu = 1.0 / nu_lab;
+      if (inner) { num = r2 - xi2; den = root - pp; }
+      else if (outward) { num = xo2 - r2; den = root + pp; }
+      else { num = root - pp; den = 1.0; }
+      const double d_shell = max0(num * rcp64(den));
+      // comoving frequencies reached at d_shell and at d_e (Thomson)
       const long long key_shell = okey(fma(-d_shell, nu_lab, nu_cmf));
-      double inv_k = 0.0, c_e = 0.0;
+      double c_e = 0.0, thr_e = 0.0;
       long long key_e = kKeyNegInf;
-      if (k > 0.0) {
-        inv_k = 1.0 / k;
-        c_e = nu_lab * inv_k;
-        key_e = okey(fma(-tau_rem, c_e, nu_cmf));
+      if (thomson) {
+        c_e = (nu_lab * s_ikap[s]) * inv_D;  // nu_lab / k, k = kappa' D
+        thr_e = fma(-tau_rem, c_e, nu_cmf);
+        key_e = okey(thr_e);
       }
       long long key_thr = key_shell > key_e ? key_shell : key_e;
       const double e_inv2 = JB ? (pk.e_lab * inv_nu) * inv_nu : 0.0;
       const size_t row = static_cast<size_t>(s) * static_cast<size_t>(L);
-      const long long *nub = reinterpret_cast<const long long *>(p.nu);
+      const double *tau_s = p.tau + row;
       int32_t j = pk.next_line;
       int kind = 0;
-      double l = 0.0;
-      // walk the redward lines while a Sobolev point is the closest event
+      double l = 0.0, nu_hit = 0.0;
+      unsigned long long rinfo_hit = 0ull;
+      long long bj = 0;
+      double taul = 0.0;
+      unsigned long long rinfo = 0ull;
+      if (j < L) {
+        bj = __ldg(nub + j);
+        taul = __ldg(tau_s + j);
+        if (MODE == 1 && p.row_info) rinfo = __ldg(p.row_info + j);
+      }
       while (j < L) {
         pk.cnt[1] += 1u;
-        const long long bj = __ldg(nub + j);
-        if (bj <= key_thr) break;
+        long long bj_n = 0;
+        double tau_n = 0.0;
+        unsigned long long rinfo_n = 0ull;
+        if (j + 1 < L) {
+          bj_n = __ldg(nub + j + 1);
+          tau_n = __ldg(tau_s + j + 1);
+          if (MODE == 1 && p.row_info) rinfo_n = __ldg(p.row_info + j + 1);
+        }
+        if (bj <= key_thr) break;  // the Sobolev point lies beyond d_shell or d_e
         pk.cnt[2] += 1u;
         const double nuj = __longlong_as_double(bj);
-        const double d_line = fmax(fma(-nuj, inv_nu, D), 0.0);
         if (JB) atomicAdd(p.j_blue + row + j, nuj * e_inv2);
-        const double taul = __ldg(p.tau + row + j);
-        if (okey(taul) > okey(fma(-k, d_line, tau_rem))) { kind = kLineEvent; l = d_line; break; }
-        tau_rem -= taul;
-        if (k > 0.0) {
-          key_e = okey(fma(-tau_rem, c_e, nu_cmf));
-          key_thr = key_shell > key_e ? key_shell : key_e;
+        bool absorbed;
+        if (thomson) {
+          const double t = fma(taul, c_e, thr_e);
+          absorbed = okey(t) > bj;
+          if (!absorbed) {
+            thr_e = t;
+            key_e = okey(t);
+            key_thr = key_shell > key_e ? key_shell : key_e;
+          }
+        } else {
+          absorbed = okey(taul) > okey(tau_rem);
+          if (!absorbed) tau_rem -= taul;
+        }
+        if (absorbed) {
+          kind = kLineEvent;
+          l = max0(fma(-nuj, inv_nu, D));
+          nu_hit = nuj;
+          rinfo_hit = rinfo;
+          break;
         }
         ++j;
+        bj = bj_n; taul = tau_n; rinfo = rinfo_n;
       }
       if (kind == 0) {
-        if (key_e > key_shell) { kind = kElectronEvent; l = tau_rem * inv_k; }
+        if (key_e > key_shell) { kind = kElectronEvent; l = max0(fma(-thr_e, inv_nu, D)); }
         else { kind = kShellEvent; l = d_shell; }
       }
       // estimators, Eqs. 13-14 (segment-start comoving values)
-      const double wgt = (e_cmf * l) * D;
+      const double wgt = eD2 * l;
       if (s != acc_s) {
         if (acc_s >= 0) {
           atomicAdd(p.j_est + acc_s, acc_j);
@@ -211,50 +304,65 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       acc_nb = fma(wgt, nu_cmf, acc_nb);
       pk.next_line = j;
       if (kind == kShellEvent) {
+        // move to the boundary; free flight keeps q, nu_lab and E_lab
         pk.cnt[5] += 1u;
         const int32_t ns = inner ? s - 1 : s + 1;
-        const double xb = inner ? xi : xo;
-        const double inv_xb = __ldg((inner ? p.inv_x_in : p.inv_x_out) + s);
-        pk.mu = fmin(fmax((pm + l) * inv_xb, -1.0), 1.0);
-        pk.x = xb;
+        pk.p = pp + l;
+        pk.r2 = inner ? xi2 : xo2;
         pk.shell = ns;
+        pk.have_inv_D = false;
         if (ns >= S) status = 1;
         else if (ns < 0) status = 2;
       } else {
-        // move to the event point (impact parameter conserved)
-        const double q = fmax(fma(x, x, -pm * pm), 0.0);
-        const double pl = pm + l;
-        const double xn = sqrt(fma(pl, pl, q));
-        const double mun = fmin(fmax(pl / xn, -1.0), 1.0);
-        const double D1 = fma(-mun, xn, 1.0);
+        // move to the event point: x mu becomes p + l, x^2 = q + (p + l)^2
+        const double pl = pp + l;
+        const double r2n = fma(pl, pl, q);
+        const double xn = sqrt(r2n);
+        const double D1 = 1.0 - pl;
         const double e_c = pk.e_lab * D1;
-        double nu_c;
+        double nu_c, inv_nu_c;
         if (kind == kLineEvent) {
           pk.cnt[3] += 1u;
-          int32_t emit = j;
-          if (MODE == 1) emit = downbranch_pick(p, __ldg(p.line_row + j), ds.closed0());
-          nu_c = __ldg(p.nu + emit);
-          pk.next_line = emit + 1;
+          if (MODE == 1) {
+            const Emission em = downbranch_pick(p, j, rinfo_hit, ds.next_u53());
+            nu_c = em.nu;
+            inv_nu_c = em.inv_nu;
+            pk.next_line = em.line + 1;
+          } else {
+            nu_c = nu_hit;
+            inv_nu_c = rcp64(nu_hit);
+            pk.next_line = j + 1;
+          }
         } else {
           pk.cnt[4] += 1u;
           nu_c = nu_lab * D1;
+          inv_nu_c = inv_nu * rcp64(D1);
         }
-        const double mu2 = fma(2.0, ds.closed0(), -1.0);
-        const double iD2 = 1.0 / fma(-mu2, xn, 1.0);
-        pk.x = xn;
-        pk.mu = mu2;
+        // isotropic re-emission: new direction, lab values from the comoving ones
+        const double mu2 = ds.mu_isotropic();
+        const double pn = xn * mu2;
+        const double D2 = 1.0 - pn;
+        const double iD2 = rcp64(D2);
+        pk.p = pn;
+        pk.q = max0(fma(-pn, pn, r2n));
+        pk.r2 = r2n;
         pk.nu_lab = nu_c * iD2;
         pk.e_lab = e_c * iD2;
+        pk.inv_nu = inv_nu_c * D2;
+        pk.inv_D = iD2;
+        pk.have_inv_D = true;
       }
     }
     if (status != 0) {
-      st[status - 1] += 1ull;
-      st[kStSegments] += pk.cnt[0];
-      st[kStLineChecks] += pk.cnt[1];
-      st[kStResonances] += pk.cnt[2];
-      st[kStLineInteractions] += pk.cnt[3];
-      st[kStEScatters] += pk.cnt[4];
-      st[kStShellCrossings] += pk.cnt[5];
+      if (status == 1) ++n_esc;
+      else if (status == 2) ++n_reab;
+      else ++n_cap;
+      n_seg += pk.cnt[0];
+      n_chk += pk.cnt[1];
+      n_res += pk.cnt[2];
+      n_lint += pk.cnt[3];
+      n_esca += pk.cnt[4];
+      n_shell += pk.cnt[5];
       if (status == 1) {
         // bin index; underflow -> bins, overflow (or NaN) -> bins + 1
         int b;
@@ -281,6 +389,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
     atomicAdd(p.j_est + acc_s, acc_j);
     atomicAdd(p.nu_bar + acc_s, acc_nb);
   }
+  unsigned long long st[kNStats] = {n_esc, n_reab, n_cap, n_seg, n_chk, n_res, n_lint, n_esca, n_shell};
 #pragma unroll
   for (int i = 0; i < kNStats; ++i) {
     unsigned long long v = st[i];
@@ -288,38 +397,47 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if (lane == 0u && v) atomicAdd(p.stats + i, v);
   }
+  if (lane == 0u) atomicMax(p.flags + 2, global_ns());
 }
 
 template <int MODE, bool JB, bool REC>
-const void *kernel_ptr(int precision) {
-  (void)precision;
+const void *kernel_ptr() {
   return reinterpret_cast<const void *>(&transport_fp64<MODE, JB, REC>);
 }
 
 const void *select_kernel(int line_mode, int precision, bool jb, bool rec) {
+  (void)precision;
   if (line_mode == 0) {
-    if (jb) return rec ? kernel_ptr<0, true, true>(precision) : kernel_ptr<0, true, false>(precision);
-    return rec ? kernel_ptr<0, false, true>(precision) : kernel_ptr<0, false, false>(precision);
+    if (jb) return rec ? kernel_ptr<0, true, true>() : kernel_ptr<0, true, false>();
+    return rec ? kernel_ptr<0, false, true>() : kernel_ptr<0, false, false>();
   }
-  if (jb) return rec ? kernel_ptr<1, true, true>(precision) : kernel_ptr<1, true, false>(precision);
-  return rec ? kernel_ptr<1, false, true>(precision) : kernel_ptr<1, false, false>(precision);
+  if (jb) return rec ? kernel_ptr<1, true, true>() : kernel_ptr<1, true, false>();
+  return rec ? kernel_ptr<1, false, true>() : kernel_ptr<1, false, false>();
 }
+
+size_t smem_bytes(int S) { return static_cast<size_t>(kShellArrays) * S * sizeof(double); }
 
 }  // namespace
 
 int transport_block_size() { return kBlock; }
 
-cudaError_t transport_occupancy(int line_mode, int precision, bool j_blue, bool record,
+cudaError_t transport_occupancy(int line_mode, int precision, bool j_blue, bool record, int S,
                                 int *blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, select_kernel(line_mode, precision, j_blue, record), kBlock, 0);
+      blocks_per_sm, select_kernel(line_mode, precision, j_blue, record), kBlock, smem_bytes(S));
 }
 
 cudaError_t launch_transport(const TransportParams &p, int line_mode, int precision, bool j_blue,
                              bool record, int grid, int block, cudaStream_t st) {
+  const void *k = select_kernel(line_mode, precision, j_blue, record);
+  const size_t smem = smem_bytes(p.S);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+  }
   void *args[] = {const_cast<TransportParams *>(&p)};
-  return cudaLaunchKernel(select_kernel(line_mode, precision, j_blue, record), dim3(grid),
-                          dim3(block), args, 0, st);
+  return cudaLaunchKernel(k, dim3(grid), dim3(block), args, smem, st);
 }
 
 }  // namespace mcgpu

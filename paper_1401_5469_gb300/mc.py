@@ -36,7 +36,7 @@ COUNTER_NAMES = ("segments", "line_checks", "resonances", "line_interactions", "
 # Every entry point declared in include/mc_transport.h.
 EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_update_radiation_field",
             "mc_read_estimators", "mc_read_spectrum", "mc_read_packets", "mc_read_plasma",
-            "mc_read_timing", "mc_launch_count", "mc_synchronize", "mc_model_destroy",
+            "mc_read_timing", "mc_read_transport_phases", "mc_launch_count", "mc_synchronize", "mc_model_destroy",
             "mc_status_string", "mc_last_error_message", "mc_transport_noalloc")
 
 
@@ -136,6 +136,8 @@ def load(build_if_missing: bool = True):
     L.mc_read_plasma.argtypes = [vp, vp, vp, vp]
     L.mc_read_timing.restype = i32
     L.mc_read_timing.argtypes = [vp, vp]
+    L.mc_read_transport_phases.restype = i32
+    L.mc_read_transport_phases.argtypes = [vp, vp]
     L.mc_launch_count.restype = i32
     L.mc_launch_count.argtypes = [vp, P(u64)]
     L.mc_synchronize.restype = i32
@@ -212,6 +214,12 @@ def mc_read_plasma(h, t_rad=None, w=None, tau=None):
 def mc_read_timing(h):
     ms = np.zeros(3, dtype=np.float32)
     _check(load().mc_read_timing(h, _p(ms)), h)
+    return ms
+
+
+def mc_read_transport_phases(h):
+    ms = np.zeros(2, dtype=np.float32)
+    _check(load().mc_read_transport_phases(h, _p(ms)), h)
     return ms
 
 
@@ -377,6 +385,9 @@ class Model:
 
     def timing(self):
         return mc_read_timing(self.h)
+
+    def phases(self):
+        return mc_read_transport_phases(self.h)
 
     def launches(self):
         return mc_launch_count(self.h)

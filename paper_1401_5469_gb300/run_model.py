@@ -45,7 +45,9 @@ def main():
             m.update_radiation_field()
         _, st, _ = m.spectrum()
         ms = m.timing()
-        print(json.dumps({"iteration": it, "ms": [float(x) for x in ms], **st}), flush=True)
+        ph = m.phases()
+        print(json.dumps({"iteration": it, "ms": [float(x) for x in ms],
+                          "bulk_ms": float(ph[0]), "tail_ms": float(ph[1]), **st}), flush=True)
     m.close()
 
 
