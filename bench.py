@@ -193,6 +193,7 @@ def run_ours(args):
     l0 = m.launches()
     k_ms = np.zeros(3)
     stats_acc = {}
+    phase_ms = np.zeros(2)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -203,6 +204,7 @@ def run_ours(args):
         mc.mc_update_radiation_field(m.h, None, None)
         # per-kernel device times of this step (events on the model's stream)
         k_ms += m.timing()
+        phase_ms += m.phases()
         _, st, _ = m.spectrum()
         for k, v in st.items():
             stats_acc[k] = stats_acc.get(k, 0) + v
@@ -239,8 +241,9 @@ def run_ours(args):
     h2d = 2 * S * 8
     d2h = (2 * S + S * L + spec.spec_bins + 2 + 2 * S) * 8
 
+    m.close()
+    mixed = measure_mixed(spec, seed, args) if os.environ.get("BENCH_SKIP_MIXED") != "1" else None
     if rank != 0:
-        m.close()
         return 0
     ms_step = 1e3 * elapsed / args.steps
     value = ws * N * args.steps / elapsed
@@ -264,6 +267,7 @@ def run_ours(args):
         "interactions_per_s": ws * (per["line_interactions"] + per["e_scatters"]) / (ms_step * 1e-3),
         "line_checks_per_s": ws * per["line_checks"] / (ms_step * 1e-3),
         "kernel_ms": {"plasma": k_ms[0] / args.steps, "transport": k1_ms, "update": k_ms[2] / args.steps},
+        "transport_phases_ms": {"queue_drain": phase_ms[0] / args.steps, "tail": phase_ms[1] / args.steps},
         "per_step": per,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "transport_fp64",
@@ -272,10 +276,45 @@ def run_ours(args):
         "e2e": {"value": ws * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
+        "mixed_precision": mixed,
     }
     print(json.dumps(line), flush=True)
-    m.close()
     return 0
+
+
+def measure_mixed(spec, seed, args):
+    """The same iteration loop in mixed precision (binary32 distances and
+    optical depths; binary64 frequencies, resonance tests and estimators)."""
+    import torch
+    from paper_1401_5469_gb300 import mc
+    N = spec.n_packets
+    m = mc.Model(spec, precision=mc.MC_PRECISION_MIXED)
+    m.set_plasma()
+    stream = torch.cuda.current_stream()
+    it = 0
+    for _ in range(args.warmup):
+        m.run_iteration(seed, it, N, spec.t_inner)
+        mc.mc_update_radiation_field(m.h, None, None)
+        it += 1
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k_ms = np.zeros(3)
+    tail = 0.0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        m.run_iteration(seed, it, N, spec.t_inner)
+        mc.mc_update_radiation_field(m.h, None, None)
+        k_ms += m.timing()
+        tail += float(m.phases()[1])
+        it += 1
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    m.close()
+    return {"value": N * args.steps / elapsed, "unit": UNIT, "ms_per_step": 1e3 * elapsed / args.steps,
+            "kernel_ms": {"plasma": k_ms[0] / args.steps, "transport": k_ms[1] / args.steps,
+                          "update": k_ms[2] / args.steps},
+            "transport_tail_ms": tail / args.steps, "dtype": "f32/f64"}
 
 
 def main():

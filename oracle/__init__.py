@@ -103,8 +103,14 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_LIB)
+            # ORACLE_LIB: a separately built copy (used by the mutation tests)
+            override = os.environ.get("ORACLE_LIB")
+            if override:
+                path = override
+            else:
+                build()
+                path = _LIB
+            L = C.CDLL(path)
             vp, i32, i64, u32, u64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
             L.orc_log.restype = d; L.orc_log.argtypes = [d]
             L.orc_exp.restype = d; L.orc_exp.argtypes = [d]

@@ -40,7 +40,7 @@ struct mc_model {
 
   double *x_in = nullptr, *x_out = nullptr, *inv_x_in = nullptr, *inv_x_out = nullptr;
   double *kappa = nullptr, *inv_kappa = nullptr;
-  DbrRec *dbr_rec = nullptr;
+  DbrRec *dbr_rec = nullptr, *dbr_bucket = nullptr;
   unsigned long long *row_info = nullptr;
   float *kappa32 = nullptr, *x_in32 = nullptr, *x_out32 = nullptr;
   double *nu = nullptr, *tau = nullptr;
@@ -208,8 +208,9 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
     return fail(nullptr, MC_ERR_INVALID_ARG, "unknown line_mode");
   if (run->precision != MC_PRECISION_FP64 && run->precision != MC_PRECISION_MIXED)
     return fail(nullptr, MC_ERR_INVALID_ARG, "unknown precision");
-  if (run->precision == MC_PRECISION_MIXED)
-    return fail(nullptr, MC_ERR_UNSUPPORTED, "mixed precision is not built in this library version");
+  if (run->precision == MC_PRECISION_MIXED && run->line_mode == MC_LINE_DOWNBRANCH &&
+      !(atomic && atomic->dbr_offset))
+    return fail(nullptr, MC_ERR_INVALID_ARG, "mixed-precision downbranch needs the branching table");
   if (run->spec_bins == 0 || !(run->spec_nu_hi > run->spec_nu_lo) || !(run->spec_nu_lo >= 0.0))
     return fail(nullptr, MC_ERR_INVALID_ARG, "spectrum needs bins > 0 and 0 <= nu_lo < nu_hi");
   if (run->record_packets && (run->max_packets == 0 || run->max_packets >= (1ull << 32)))
@@ -306,7 +307,8 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
   const size_t SL = static_cast<size_t>(S) * L;
   bool ok = alloc_n(m, &m->x_in, S) && alloc_n(m, &m->x_out, S) && alloc_n(m, &m->inv_x_in, S) &&
             alloc_n(m, &m->inv_x_out, S) && alloc_n(m, &m->kappa, S) && alloc_n(m, &m->inv_kappa, S) && alloc_n(m, &m->nu, L) &&
-            alloc_n(m, &m->tau, SL) && alloc_n(m, &m->t_rad, S) && alloc_n(m, &m->w, S) &&
+            (run->precision == MC_PRECISION_MIXED ? alloc_n(m, &m->tau32, SL) : alloc_n(m, &m->tau, SL)) &&
+            alloc_n(m, &m->t_rad, S) && alloc_n(m, &m->w, S) &&
             alloc_n(m, &m->norm, S) && alloc_n(m, &m->j_est, S) && alloc_n(m, &m->nu_bar, S) &&
             alloc_n(m, &m->spectrum, static_cast<size_t>(run->spec_bins) + 2) &&
             alloc_n(m, &m->counters, static_cast<size_t>(kNCounterSlots)) &&
@@ -322,7 +324,8 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
       ok = alloc_n(m, &m->dbr_offset, IK + 1) && alloc_n(m, &m->dbr_line, nnz) &&
            alloc_n(m, &m->dbr_cdf, nnz);
     if (ok && atomic->dbr_offset && meta && run->line_mode == MC_LINE_DOWNBRANCH)
-      ok = alloc_n(m, &m->dbr_rec, nnz) && alloc_n(m, &m->row_info, L);
+      ok = alloc_n(m, &m->dbr_rec, nnz) && alloc_n(m, &m->dbr_bucket, nnz) &&
+           alloc_n(m, &m->row_info, L);
   }
   if (ok && run->record_packets) {
     const size_t n = run->max_packets;
@@ -403,7 +406,8 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
     m->launches += 1;
     if (m->dbr_rec) {
       chk(launch_dbr_setup(static_cast<uint32_t>(nnz), I * K, L, Kc, m->dbr_offset, m->dbr_line,
-                           m->dbr_cdf, m->nu, m->line_row, m->dbr_rec, m->row_info, m->stream));
+                           m->dbr_cdf, m->nu, m->line_row, m->dbr_rec, m->dbr_bucket,
+                           m->row_info, m->stream));
       m->launches += 2;
     }
     // Host buffers of the staged copies must outlive the async copies.
@@ -454,7 +458,15 @@ mc_status mc_set_plasma(mc_model *m, const double *t_rad, const double *w, const
     const size_t SL = static_cast<size_t>(S) * m->L;
     for (size_t i = 0; i < SL; ++i)
       if (!std::isfinite(tau[i])) return fail(m, MC_ERR_INVALID_ARG, "tau must be finite");
-    if (e == cudaSuccess) e = upload(m, m->tau, tau, SL);
+    if (m->tau32) {
+      // mixed precision keeps binary32 depths only
+      std::vector<float> t32(SL);
+      for (size_t i = 0; i < SL; ++i) t32[i] = static_cast<float>(tau[i]);
+      if (e == cudaSuccess) e = upload(m, m->tau32, t32.data(), SL);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    } else if (e == cudaSuccess) {
+      e = upload(m, m->tau, tau, SL);
+    }
     m->tau_given = true;
     m->tau_dirty = false;
   } else {
@@ -498,6 +510,7 @@ mc_status mc_run_iteration(mc_model *m, uint64_t seed, uint32_t iteration, uint6
   p.L = static_cast<int32_t>(m->L);
   p.x_in = m->x_in; p.x_out = m->x_out; p.inv_x_in = m->inv_x_in; p.inv_x_out = m->inv_x_out;
   p.inv_kappa = m->inv_kappa; p.row_info = m->row_info; p.dbr_rec = m->dbr_rec;
+  p.dbr_bucket = m->dbr_bucket;
   p.kappa = m->kappa; p.kappa32 = m->kappa32; p.x_in32 = m->x_in32; p.x_out32 = m->x_out32;
   p.nu = m->nu; p.tau = m->tau; p.tau32 = m->tau32;
   p.line_row = m->line_row; p.dbr_offset = m->dbr_offset; p.dbr_line = m->dbr_line; p.dbr_cdf = m->dbr_cdf;
@@ -632,10 +645,20 @@ mc_status mc_read_plasma(mc_model *m, double *t_rad, double *w, double *tau) {
   cudaError_t e = cudaSuccess;
   if (t_rad) e = cudaMemcpyAsync(t_rad, m->t_rad, m->S * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess && w) e = cudaMemcpyAsync(w, m->w, m->S * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
-  if (e == cudaSuccess && tau)
-    e = cudaMemcpyAsync(tau, m->tau, static_cast<size_t>(m->S) * m->L * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+  const size_t SL = static_cast<size_t>(m->S) * m->L;
+  std::vector<float> t32;
+  if (e == cudaSuccess && tau) {
+    if (m->tau32) {
+      t32.resize(SL);
+      e = cudaMemcpyAsync(t32.data(), m->tau32, SL * sizeof(float), cudaMemcpyDeviceToHost, m->stream);
+    } else {
+      e = cudaMemcpyAsync(tau, m->tau, SL * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+    }
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) return cuda_fail(m, e, "read plasma");
+  if (tau && m->tau32)
+    for (size_t i = 0; i < SL; ++i) tau[i] = static_cast<double>(t32[i]);
   return MC_OK;
 }
 

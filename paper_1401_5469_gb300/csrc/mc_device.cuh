@@ -48,9 +48,17 @@ struct DrawStream {
   __device__ __forceinline__ double open0() { return __ull2double_rn(next_u53() + 1ull) * 0x1.0p-53; }
   // z in [0, 1)
   __device__ __forceinline__ double closed0() { return __ull2double_rn(next_u53()) * 0x1.0p-53; }
-  // mu = 2 z - 1 for z = u53 2^-53 in [0, 1): (u53 - 2^52) 2^-52, exact
+  // mu = 2 z - 1 for z = u53 2^-53 in [0, 1): (u53 - 2^52) 2^-52, exact.
+  // Assembled from the integer's bits (no conversion instruction).
   __device__ __forceinline__ double mu_isotropic() {
-    return __ll2double_rn(static_cast<long long>(next_u53()) - (1ll << 52)) * 0x1.0p-52;
+    const long long v = static_cast<long long>(next_u53()) - (1ll << 52);
+    const unsigned long long a = static_cast<unsigned long long>(v < 0 ? -v : v);  // <= 2^52
+    if (a == 0ull) return 0.0;
+    const int lz = __clzll(static_cast<long long>(a));
+    const unsigned long long mant = ((a << lz) << 1) >> 12;
+    const unsigned long long bits = (static_cast<unsigned long long>(63 - lz - 52 + 1023) << 52) |
+                                    mant | (v < 0 ? (1ull << 63) : 0ull);
+    return __longlong_as_double(static_cast<long long>(bits));
   }
 };
 
@@ -114,12 +122,38 @@ __device__ __forceinline__ double log_core(int k, unsigned long long frac) {
   return fma(dk, kLn2Head, ct.y) + fma(p, r, dk * kLn2Tail);
 }
 
-// -ln(z) for z = u 2^-53, 1 <= u <= 2^53 (the (0,1] draw), integer-only reduction.
+#define MC_KLN2(k) {(k) * kLn2Head, (k) * kLn2Tail}
+#define MC_KLN2_8(b) MC_KLN2(b), MC_KLN2(b - 1), MC_KLN2(b - 2), MC_KLN2(b - 3), \
+                     MC_KLN2(b - 4), MC_KLN2(b - 5), MC_KLN2(b - 6), MC_KLN2(b - 7)
+// {k ln2 head, k ln2 tail} for k = 0, -1, ..., -55 (both products exact / correctly rounded).
+static __constant__ double2 c_kln2[56] = {MC_KLN2_8(0), MC_KLN2_8(-8), MC_KLN2_8(-16), MC_KLN2_8(-24),
+                                          MC_KLN2_8(-32), MC_KLN2_8(-40), MC_KLN2_8(-48)};
+#undef MC_KLN2_8
+#undef MC_KLN2
+
+// -ln(z) for z = u 2^-53, 1 <= u <= 2^53 (the (0,1] draw): integer-only
+// reduction, k ln2 from a table (no conversion instruction), then Tang's
+// method as in log_core.
 __device__ __forceinline__ double neg_log_u53(unsigned long long u) {
   const int lz = __clzll(static_cast<long long>(u));
-  const int e = 63 - lz;
   const unsigned long long frac = ((u << lz) << 1) >> 12;
-  return -log_core(e - 53, frac);
+  int k = 63 - lz - 53;  // in [-53, 0]
+  const int i = static_cast<int>(frac >> 45);
+  long long mb = static_cast<long long>(0x3ff0000000000000ull | frac);
+  if (i >= 64) { mb -= (1ll << 52); ++k; }
+  const double m = __longlong_as_double(mb);
+  const double2 ct = c_log_tab[i];
+  const double2 kl = c_kln2[-k];
+  const double r = fma(m, ct.x, -1.0);
+  double p = -0.125;
+  p = fma(p, r, 1.0 / 7.0);
+  p = fma(p, r, -1.0 / 6.0);
+  p = fma(p, r, 0.2);
+  p = fma(p, r, -0.25);
+  p = fma(p, r, 1.0 / 3.0);
+  p = fma(p, r, -0.5);
+  p = fma(p, r, 1.0);
+  return -((kl.x + ct.y) + fma(p, r, kl.y));
 }
 
 // ln(x) for a positive normal binary64 x.

@@ -58,6 +58,8 @@ struct TransportParams {
   const double *inv_kappa;           // [S] 1/kappa (0 where kappa = 0), or nullptr
   const unsigned long long *row_info;// [L] row begin | row length << 32, or nullptr
   const DbrRec *dbr_rec;             // [nnz] guide-table rows, or nullptr
+  const DbrRec *dbr_bucket;          // [nnz] bucket k of a row: copy of its guide entry's
+                                     // record, guide field = that entry's position
   double *j_est, *nu_bar;            // [S] raw sums
   double *j_blue;                    // [S*L] raw sums or nullptr
   double *spectrum;                  // [bins + 2]
@@ -110,6 +112,9 @@ cudaError_t launch_transport(const TransportParams &p, int line_mode, int precis
 int transport_block_size();
 cudaError_t transport_occupancy(int line_mode, int precision, bool j_blue, bool record, int S,
                                 int *blocks_per_sm);
+const void *select_mixed_kernel(int line_mode, bool j_blue, bool record);
+size_t mixed_smem_bytes(int S);
+cudaError_t launch_to_f32(const double *in, float *out, size_t n, cudaStream_t st);
 cudaError_t launch_populations(const PlasmaParams &p, cudaStream_t st);
 cudaError_t launch_sobolev_tau(const PlasmaParams &p, cudaStream_t st);
 cudaError_t launch_update(const UpdateParams &p, cudaStream_t st);
@@ -119,7 +124,8 @@ cudaError_t launch_zero_large(double *a, size_t n, cudaStream_t st);
 cudaError_t launch_dbr_setup(uint32_t nnz, uint32_t n_rows, uint32_t L, int K,
                              const uint32_t *dbr_offset, const uint32_t *dbr_line,
                              const double *dbr_cdf, const double *nu, const int32_t *line_row,
-                             DbrRec *rec, unsigned long long *row_info, cudaStream_t st);
+                             DbrRec *rec, DbrRec *bucket, unsigned long long *row_info,
+                             cudaStream_t st);
 cudaError_t launch_line_setup(int L, int K, const double *nu, const double *f, const int32_t *ion,
                               const int32_t *lower, const int32_t *upper, const double *g,
                               double t_exp, int32_t *lev_l, int32_t *lev_u, double *pref,

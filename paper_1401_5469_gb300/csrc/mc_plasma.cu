@@ -137,6 +137,24 @@ __global__ void dbr_rec_kernel(uint32_t nnz, uint32_t n_rows, const uint32_t *of
   rec[e].guide = a;
 }
 
+// Bucket slots: slot b + k holds the record of the row's guide entry G[k],
+// with its guide field set to G[k].
+__global__ void dbr_bucket_kernel(uint32_t nnz, uint32_t n_rows, const uint32_t *off,
+                                  const DbrRec *rec, DbrRec *bucket) {
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  uint32_t lo = 0, hi = n_rows;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (off[mid] <= e) lo = mid; else hi = mid;
+  }
+  const uint32_t b = off[lo];
+  const uint32_t g = rec[e].guide;
+  DbrRec r = rec[b + g];
+  r.guide = g;
+  bucket[e] = r;
+}
+
 __global__ void row_info_kernel(uint32_t L, const int32_t *line_row, const uint32_t *off,
                                 unsigned long long *row_info) {
   const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,6 +162,12 @@ __global__ void row_info_kernel(uint32_t L, const int32_t *line_row, const uint3
   const int32_t r = line_row[j];
   const unsigned long long b = off[r], n = off[r + 1] - off[r];
   row_info[j] = b | (n << 32);
+}
+
+__global__ void to_f32_kernel(const double *in, float *out, size_t n) {
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n; i += stride)
+    out[i] = static_cast<float>(in[i]);
 }
 
 int sm_count() {
@@ -199,13 +223,21 @@ cudaError_t launch_line_setup(int L, int K, const double *nu, const double *f, c
 cudaError_t launch_dbr_setup(uint32_t nnz, uint32_t n_rows, uint32_t L, int K,
                              const uint32_t *dbr_offset, const uint32_t *dbr_line,
                              const double *dbr_cdf, const double *nu, const int32_t *line_row,
-                             DbrRec *rec, unsigned long long *row_info, cudaStream_t st) {
+                             DbrRec *rec, DbrRec *bucket, unsigned long long *row_info,
+                             cudaStream_t st) {
   (void)K;
-  if (nnz > 0)
+  if (nnz > 0) {
     dbr_rec_kernel<<<(nnz + 255) / 256, 256, 0, st>>>(nnz, n_rows, dbr_offset, dbr_line, dbr_cdf, nu, rec);
+    dbr_bucket_kernel<<<(nnz + 255) / 256, 256, 0, st>>>(nnz, n_rows, dbr_offset, rec, bucket);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   row_info_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, line_row, dbr_offset, row_info);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double *in, float *out, size_t n, cudaStream_t st) {
+  to_f32_kernel<<<sm_count() * 8, 256, 0, st>>>(in, out, n);
   return cudaGetLastError();
 }
 

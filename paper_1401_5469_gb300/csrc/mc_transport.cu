@@ -73,11 +73,21 @@ __device__ __forceinline__ Emission downbranch_pick(const TransportParams &p, in
                                                     unsigned long long rinfo, unsigned long long u) {
   Emission em;
   if (p.dbr_rec) {
+    // bucket slot: a copy of the guide entry's record, so that the common case
+    // (the guide entry is the answer) is a single 32-byte load
     const uint32_t b = static_cast<uint32_t>(rinfo), len = static_cast<uint32_t>(rinfo >> 32);
     const uint32_t bucket = static_cast<uint32_t>(__umul64hi(u << 11, static_cast<unsigned long long>(len)));
+    const DbrRec *slot = p.dbr_bucket + b + bucket;
+    unsigned long long thr = __ldg(&slot->thr);
+    if (u < thr) {
+      em.nu = __ldg(&slot->nu);
+      em.inv_nu = __ldg(&slot->inv_nu);
+      em.line = static_cast<int32_t>(__ldg(&slot->emit));
+      return em;
+    }
     const DbrRec *rec = p.dbr_rec;
-    uint32_t i = b + __ldg(&rec[b + bucket].guide);
-    unsigned long long thr = __ldg(&rec[i].thr);
+    uint32_t i = b + __ldg(&slot->guide) + 1u;
+    thr = __ldg(&rec[i].thr);
     while (u >= thr) { ++i; thr = __ldg(&rec[i].thr); }
     em.nu = __ldg(&rec[i].nu);
     em.inv_nu = __ldg(&rec[i].inv_nu);
@@ -215,18 +225,14 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       const bool thomson = kap > 0.0;
       // optical depth to the next event, tau = -ln z
       double tau_rem = neg_log_u53(ds.next_u53() + 1ull);
-      // distance to the shell boundary (cancellation-free roots)
+      // Shell boundary: at the exit point x mu = p_exit = +-sqrt(x_b^2 - q) (the
+      // inner sphere is hit when moving inward with q <= x_in^2), so the path
+      // length is p_exit - p and the comoving frequency there nu_lab (1 - p_exit).
       const double xi2 = s_xi2[s], xo2 = s_xo2[s];
-      const bool outward = pp >= 0.0;
-      const bool inner = !outward && okey(q) <= okey(xi2);
+      const bool inner = okey(pp) < -1 && okey(q) <= okey(xi2);  // p < 0 (not -0)
       const double root = sqrt((inner ? xi2 : xo2) - q);
-      double num, den;
-      if (inner) { num = r2 - xi2; den = root - pp; }
-      else if (outward) { num = xo2 - r2; den = root + pp; }
-      else { num = root - pp; den = 1.0; }
-      const double d_shell = max0(num * rcp64(den));
-      // comoving frequencies reached at d_shell and at d_e (Thomson)
-      const long long key_shell = okey(fma(-d_shell, nu_lab, nu_cmf));
+      const double p_exit = inner ? -root : root;
+      const long long key_shell = okey(nu_lab * (1.0 - p_exit));
       double c_e = 0.0, thr_e = 0.0;
       long long key_e = kKeyNegInf;
       if (thomson) {
@@ -242,23 +248,29 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       int kind = 0;
       double l = 0.0, nu_hit = 0.0;
       unsigned long long rinfo_hit = 0ull;
-      long long bj = 0;
-      double taul = 0.0;
-      unsigned long long rinfo = 0ull;
+      // two lines ahead are always in flight while line j is resolved
+      long long bj = 0, bj_n = 0;
+      double taul = 0.0, tau_n = 0.0;
+      unsigned long long rinfo = 0ull, rinfo_n = 0ull;
       if (j < L) {
         bj = __ldg(nub + j);
         taul = __ldg(tau_s + j);
         if (MODE == 1 && p.row_info) rinfo = __ldg(p.row_info + j);
       }
+      if (j + 1 < L) {
+        bj_n = __ldg(nub + j + 1);
+        tau_n = __ldg(tau_s + j + 1);
+        if (MODE == 1 && p.row_info) rinfo_n = __ldg(p.row_info + j + 1);
+      }
       while (j < L) {
         pk.cnt[1] += 1u;
-        long long bj_n = 0;
-        double tau_n = 0.0;
-        unsigned long long rinfo_n = 0ull;
-        if (j + 1 < L) {
-          bj_n = __ldg(nub + j + 1);
-          tau_n = __ldg(tau_s + j + 1);
-          if (MODE == 1 && p.row_info) rinfo_n = __ldg(p.row_info + j + 1);
+        long long bj_nn = 0;
+        double tau_nn = 0.0;
+        unsigned long long rinfo_nn = 0ull;
+        if (j + 2 < L) {
+          bj_nn = __ldg(nub + j + 2);
+          tau_nn = __ldg(tau_s + j + 2);
+          if (MODE == 1 && p.row_info) rinfo_nn = __ldg(p.row_info + j + 2);
         }
         if (bj <= key_thr) break;  // the Sobolev point lies beyond d_shell or d_e
         pk.cnt[2] += 1u;
@@ -286,10 +298,11 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         }
         ++j;
         bj = bj_n; taul = tau_n; rinfo = rinfo_n;
+        bj_n = bj_nn; tau_n = tau_nn; rinfo_n = rinfo_nn;
       }
       if (kind == 0) {
         if (key_e > key_shell) { kind = kElectronEvent; l = max0(fma(-thr_e, inv_nu, D)); }
-        else { kind = kShellEvent; l = d_shell; }
+        else { kind = kShellEvent; l = max0(p_exit - pp); }
       }
       // estimators, Eqs. 13-14 (segment-start comoving values)
       const double wgt = eD2 * l;
@@ -307,7 +320,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         // move to the boundary; free flight keeps q, nu_lab and E_lab
         pk.cnt[5] += 1u;
         const int32_t ns = inner ? s - 1 : s + 1;
-        pk.p = pp + l;
+        pk.p = p_exit;
         pk.r2 = inner ? xi2 : xo2;
         pk.shell = ns;
         pk.have_inv_D = false;
@@ -406,7 +419,7 @@ const void *kernel_ptr() {
 }
 
 const void *select_kernel(int line_mode, int precision, bool jb, bool rec) {
-  (void)precision;
+  if (precision == 1) return select_mixed_kernel(line_mode, jb, rec);
   if (line_mode == 0) {
     if (jb) return rec ? kernel_ptr<0, true, true>() : kernel_ptr<0, true, false>();
     return rec ? kernel_ptr<0, false, true>() : kernel_ptr<0, false, false>();
@@ -415,7 +428,9 @@ const void *select_kernel(int line_mode, int precision, bool jb, bool rec) {
   return rec ? kernel_ptr<1, false, true>() : kernel_ptr<1, false, false>();
 }
 
-size_t smem_bytes(int S) { return static_cast<size_t>(kShellArrays) * S * sizeof(double); }
+size_t smem_bytes(int S, int precision) {
+  return precision == 1 ? mixed_smem_bytes(S) : static_cast<size_t>(kShellArrays) * S * sizeof(double);
+}
 
 }  // namespace
 
@@ -424,13 +439,14 @@ int transport_block_size() { return kBlock; }
 cudaError_t transport_occupancy(int line_mode, int precision, bool j_blue, bool record, int S,
                                 int *blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, select_kernel(line_mode, precision, j_blue, record), kBlock, smem_bytes(S));
+      blocks_per_sm, select_kernel(line_mode, precision, j_blue, record), kBlock,
+      smem_bytes(S, precision));
 }
 
 cudaError_t launch_transport(const TransportParams &p, int line_mode, int precision, bool j_blue,
                              bool record, int grid, int block, cudaStream_t st) {
   const void *k = select_kernel(line_mode, precision, j_blue, record);
-  const size_t smem = smem_bytes(p.S);
+  const size_t smem = smem_bytes(p.S, precision);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));

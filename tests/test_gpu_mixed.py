@@ -1,0 +1,70 @@
+"""Mixed precision (binary32 distances and optical depths, binary64
+frequencies, resonance comparisons and estimator sums) against the binary64
+path.
+
+Mixed-precision packets follow the same random draws, but their histories
+diverge once a binary32 rounding flips a decision, so agreement is judged
+against the Monte Carlo noise: the per-shell J and nu_bar estimators, the
+escaped energy and the interaction counts of the mixed run must lie within 5
+standard deviations (estimated from 8 independent-seed binary64 runs) of the
+binary64 run with the same seed, and the CPU oracle's run with that seed must
+lie within the same band.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_5469_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1401_5469_gb300 import mc as mcmod
+    mcmod.load()
+    return mcmod
+
+
+def _run(mc, spec, tau, precision, seed, n):
+    m = mc.Model(spec, precision=precision)
+    m.set_plasma(tau=tau)
+    m.run_iteration(seed, 0, n, spec.t_inner)
+    j, nb, _, norm = m.estimators()
+    sp, st, _ = m.spectrum()
+    m.close()
+    return j * norm, nb * norm, sp, st
+
+
+@pytest.mark.parametrize("kind", ["scatter", "downbranch"])
+def test_mixed_within_monte_carlo_noise(mc, kind):
+    if kind == "scatter":
+        spec = synth.scatter_model(n_lines=2000, n_packets=40_000)
+        tau = spec.tau
+    else:
+        spec = synth.downbranch_model(n_lines=20_000, n_packets=20_000)
+        tau = oracle.plasma_tau(spec, np.full(spec.n_shells, 1.0e4), oracle.geometric_dilution(spec))
+    n = spec.n_packets
+    ref = [_run(mc, spec, tau, mc.MC_PRECISION_FP64, 5469 + k, n) for k in range(8)]
+    J = np.array([r[0] for r in ref])
+    NB = np.array([r[1] for r in ref])
+    ESC = np.array([r[2][:-2].sum() + r[2][-2] + r[2][-1] for r in ref])
+    sJ, sNB, sE = J.std(0, ddof=1), NB.std(0, ddof=1), ESC.std(ddof=1)
+    j64, nb64, sp64, st64 = ref[0]
+    j32, nb32, sp32, st32 = _run(mc, spec, tau, mc.MC_PRECISION_MIXED, 5469, n)
+    keep = sJ > 0
+    assert np.all(np.abs(j32 - j64)[keep] <= 5 * sJ[keep] + 1e-12 * np.abs(j64[keep]))
+    assert np.all(np.abs(nb32 - nb64)[keep] <= 5 * sNB[keep] + 1e-12 * np.abs(nb64[keep]))
+    e32 = sp32[:-2].sum() + sp32[-2] + sp32[-1]
+    assert abs(e32 - ESC[0]) <= 5 * sE + 1e-12 * ESC[0]
+    for key in ("line_interactions", "segments"):
+        vals = np.array([r[3][key] for r in ref], dtype=float)
+        assert abs(st32[key] - st64[key]) <= 5 * vals.std(ddof=1) + 1
+    # the FP64 oracle with the same seed sits in the same band
+    om = oracle.OracleModel(spec, tau=tau)
+    r = oracle.run_iteration(om, 5469, 0, n, spec.t_inner, record=False, threads=4)
+    norm = oracle.estimator_norm(spec)
+    assert np.all(np.abs(r.j_est * norm - j32)[keep] <= 5 * sJ[keep] + 1e-12 * np.abs(j64[keep]))
