@@ -171,6 +171,18 @@ mc_status mc_set_plasma(mc_model *m, const double *t_rad, const double *w, const
 mc_status mc_run_iteration(mc_model *m, uint64_t seed, uint32_t iteration, uint64_t n_packets,
                            double t_inner);
 
+/* Packets [first_packet, first_packet + n_packets) of an iteration of n_total
+ * packets (packet energy E = L_i dt / n_total, Eq. 10); the random draws of a
+ * packet depend only on (seed, iteration, packet id), so disjoint ranges run
+ * on different devices or at different times reproduce the whole iteration.
+ * Estimators and spectrum hold the sums over this range; packet records are
+ * indexed from first_packet.  mc_run_iteration(m, s, it, n, T) is
+ * mc_run_iteration_range(m, s, it, 0, n, n, T).
+ *  Errors: MC_ERR_INVALID_ARG (empty range, first + n_packets > n_total,
+ *  n_total >= 2^32, records too small), MC_ERR_NOT_READY. */
+mc_status mc_run_iteration_range(mc_model *m, uint64_t seed, uint32_t iteration, uint64_t first_packet,
+                                 uint64_t n_packets, uint64_t n_total, double t_inner);
+
 /* Update T_R and W from the last run's estimators (Eqs. 15-16) on the device;
  * shells with no path length keep their values.  The next run recomputes the
  * Sobolev depths when they are not given.  Copies the new values to t_rad_out

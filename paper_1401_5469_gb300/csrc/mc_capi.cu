@@ -481,9 +481,16 @@ mc_status mc_set_plasma(mc_model *m, const double *t_rad, const double *w, const
 
 mc_status mc_run_iteration(mc_model *m, uint64_t seed, uint32_t iteration, uint64_t n_packets,
                            double t_inner) {
+  return mc_run_iteration_range(m, seed, iteration, 0, n_packets, n_packets, t_inner);
+}
+
+mc_status mc_run_iteration_range(mc_model *m, uint64_t seed, uint32_t iteration, uint64_t first_packet,
+                                 uint64_t n_packets, uint64_t n_total, double t_inner) {
   if (!m) return MC_ERR_INVALID_ARG;
   if (!m->plasma_set) return fail(m, MC_ERR_NOT_READY, "mc_set_plasma has not been called");
-  if (n_packets == 0 || n_packets >= (1ull << 32)) return fail(m, MC_ERR_INVALID_ARG, "need 0 < n_packets < 2^32");
+  if (n_packets == 0 || n_total >= (1ull << 32) || first_packet + n_packets > n_total ||
+      first_packet + n_packets < first_packet)
+    return fail(m, MC_ERR_INVALID_ARG, "need 0 < n_packets, first + n_packets <= n_total < 2^32");
   if (m->run.record_packets && n_packets > m->run.max_packets)
     return fail(m, MC_ERR_INVALID_ARG, "n_packets exceeds max_packets of the packet records");
   if (!(t_inner > 0.0) || !std::isfinite(t_inner)) return fail(m, MC_ERR_INVALID_ARG, "t_inner must be positive");
@@ -523,13 +530,14 @@ mc_status mc_run_iteration(mc_model *m, uint64_t seed, uint32_t iteration, uint6
   p.spec_hi = m->run.spec_nu_hi;
   p.spec_dnu = (m->run.spec_nu_hi - m->run.spec_nu_lo) / static_cast<double>(m->run.spec_bins);
   p.n_packets = n_packets;
+  p.first_packet = first_packet;
   p.iteration = iteration;
   p.key0 = static_cast<uint32_t>(seed);
   p.key1 = static_cast<uint32_t>(seed >> 32);
   // Eqs. 9-10: E = 4 pi r_i^2 sigma T^4 dt / N (comoving, equal for all packets).
   const double r_i = m->r_inner;
   const double lum = (((4.0 * kPi) * r_i) * r_i) * kSigmaSB * t_inner * t_inner * t_inner * t_inner;
-  p.e_cmf = (lum * m->run.delta_t) / static_cast<double>(n_packets);
+  p.e_cmf = (lum * m->run.delta_t) / static_cast<double>(n_total);
   p.nu_scale = (kKB * t_inner) / kH;
   p.planck_cdf = m->planck_cdf;
   p.max_segments = m->run.max_segments;

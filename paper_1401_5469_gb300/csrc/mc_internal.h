@@ -66,7 +66,8 @@ struct TransportParams {
   unsigned long long *stats;         // [kNStats]
   int32_t spec_bins;
   double spec_lo, spec_hi, spec_dnu;
-  uint64_t n_packets;
+  uint64_t n_packets;                // packets of this launch
+  uint64_t first_packet;             // global id of the first (records are relative)
   uint32_t iteration, key0, key1;
   double e_cmf;                      // comoving packet energy, Eq. 10
   double nu_scale;                   // k T_inner / h

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       if (need) {
         const unsigned long long id = base + __popc(needmask & lanemask_lt);
         if (id < p.n_packets) {
-          pk.pid = static_cast<uint32_t>(id);
+          pk.pid = static_cast<uint32_t>(p.first_packet + id);
           ds.init(p.key0, p.key1, pk.pid, p.iteration);
           inject(p, p.planck_cdf, x0, x0sq, pk, ds);
           alive = true;
@@ -388,12 +388,12 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         atomicAdd(p.spectrum + b, pk.e_lab);
       }
       if (REC) {
-        p.rec_status[pk.pid] = status;
-        p.rec_nu[pk.pid] = pk.nu_lab;
-        p.rec_e[pk.pid] = pk.e_lab;
+        p.rec_status[pk.pid - p.first_packet] = status;
+        p.rec_nu[pk.pid - p.first_packet] = pk.nu_lab;
+        p.rec_e[pk.pid - p.first_packet] = pk.e_lab;
 #pragma unroll
         for (int c = 0; c < kNCounters; ++c)
-          p.rec_cnt[static_cast<size_t>(pk.pid) * kNCounters + c] = pk.cnt[c];
+          p.rec_cnt[static_cast<size_t>(pk.pid - p.first_packet) * kNCounters + c] = pk.cnt[c];
       }
       alive = false;
     }

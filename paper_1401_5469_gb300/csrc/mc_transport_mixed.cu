@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
   int32_t acc_s = -1;
   double acc_j = 0.0, acc_nb = 0.0;
   const long long *nub = reinterpret_cast<const long long *>(p.nu);
-  const float e_cmf0 = static_cast<float>(p.e_cmf);
+  const double e_cmf0 = p.e_cmf;  // binary32 energies are carried relative to this
 
   for (;;) {
     const bool need = !alive && !finished;
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         const unsigned long long id = base + __popc(needmask & lanemask_lt);
         if (id < p.n_packets) {
           // injection (Sect. 2.4), same draws as the binary64 kernel
-          pk.pid = static_cast<uint32_t>(id);
+          pk.pid = static_cast<uint32_t>(p.first_packet + id);
           ds.init(p.key0, p.key1, pk.pid, p.iteration);
           const double z0 = ds.closed0();
           const double z1 = ds.open0(), z2 = ds.open0(), z3 = ds.open0(), z4 = ds.open0();
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
           pk.r2 = x0sq;
           pk.q = max0f(fmaf(-pp, pp, x0sq));
           pk.nu_lab = nu_cmf * static_cast<double>(iD);
-          pk.e_lab = e_cmf0 * iD;
+          pk.e_lab = iD;  // E_lab / E_cmf(injection)
           pk.inv_nu = static_cast<float>(1.0 / nu_cmf) * D;
           pk.inv_D = iD;
           pk.have_inv_D = true;
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         if (bj <= key_thr) break;
         pk.cnt[2] += 1u;
         const double nuj = __longlong_as_double(bj);
-        if (JB) atomicAdd(p.j_blue + row + j, static_cast<double>(static_cast<float>(nuj) * e_inv2));
+        if (JB) atomicAdd(p.j_blue + row + j, static_cast<double>(static_cast<float>(nuj) * e_inv2) * e_cmf0);
         bool absorbed;
         if (thomson) {
           const double t = thr_e + static_cast<double>(taul * c_e);
@@ -258,8 +258,8 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
       const double wgt = static_cast<double>(eD2 * l);
       if (s != acc_s) {
         if (acc_s >= 0) {
-          atomicAdd(p.j_est + acc_s, acc_j);
-          atomicAdd(p.nu_bar + acc_s, acc_nb);
+          atomicAdd(p.j_est + acc_s, acc_j * e_cmf0);
+          atomicAdd(p.nu_bar + acc_s, acc_nb * e_cmf0);
         }
         acc_s = s; acc_j = 0.0; acc_nb = 0.0;
       }
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
       n_lint += pk.cnt[3];
       n_esca += pk.cnt[4];
       n_shell += pk.cnt[5];
-      const double e_lab = static_cast<double>(pk.e_lab);
+      const double e_lab = static_cast<double>(pk.e_lab) * e_cmf0;
       if (status == 1) {
         int b;
         if (pk.nu_lab < p.spec_lo) b = p.spec_bins;
@@ -339,19 +339,19 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         atomicAdd(p.spectrum + b, e_lab);
       }
       if (REC) {
-        p.rec_status[pk.pid] = status;
-        p.rec_nu[pk.pid] = pk.nu_lab;
-        p.rec_e[pk.pid] = e_lab;
+        p.rec_status[pk.pid - p.first_packet] = status;
+        p.rec_nu[pk.pid - p.first_packet] = pk.nu_lab;
+        p.rec_e[pk.pid - p.first_packet] = e_lab;
 #pragma unroll
         for (int c = 0; c < kNCounters; ++c)
-          p.rec_cnt[static_cast<size_t>(pk.pid) * kNCounters + c] = pk.cnt[c];
+          p.rec_cnt[static_cast<size_t>(pk.pid - p.first_packet) * kNCounters + c] = pk.cnt[c];
       }
       alive = false;
     }
   }
   if (acc_s >= 0) {
-    atomicAdd(p.j_est + acc_s, acc_j);
-    atomicAdd(p.nu_bar + acc_s, acc_nb);
+    atomicAdd(p.j_est + acc_s, acc_j * e_cmf0);
+    atomicAdd(p.nu_bar + acc_s, acc_nb * e_cmf0);
   }
   unsigned long long st[kNStats] = {n_esc, n_reab, n_cap, n_seg, n_chk, n_res, n_lint, n_esca, n_shell};
 #pragma unroll

@@ -34,7 +34,8 @@ COUNTER_NAMES = ("segments", "line_checks", "resonances", "line_interactions", "
                  "shell_crossings")
 
 # Every entry point declared in include/mc_transport.h.
-EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_update_radiation_field",
+EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_run_iteration_range",
+            "mc_update_radiation_field",
             "mc_read_estimators", "mc_read_spectrum", "mc_read_packets", "mc_read_plasma",
             "mc_read_timing", "mc_read_transport_phases", "mc_launch_count", "mc_synchronize", "mc_model_destroy",
             "mc_status_string", "mc_last_error_message", "mc_transport_noalloc")
@@ -124,6 +125,8 @@ def load(build_if_missing: bool = True):
     L.mc_set_plasma.argtypes = [vp, vp, vp, vp]
     L.mc_run_iteration.restype = i32
     L.mc_run_iteration.argtypes = [vp, u64, u32, u64, d]
+    L.mc_run_iteration_range.restype = i32
+    L.mc_run_iteration_range.argtypes = [vp, u64, u32, u64, u64, u64, d]
     L.mc_update_radiation_field.restype = i32
     L.mc_update_radiation_field.argtypes = [vp, vp, vp]
     L.mc_read_estimators.restype = i32
@@ -189,6 +192,11 @@ def mc_set_plasma(h, t_rad=None, w=None, tau=None):
 
 def mc_run_iteration(h, seed, iteration, n_packets, t_inner):
     return _check(load().mc_run_iteration(h, seed, iteration, n_packets, float(t_inner)), h)
+
+
+def mc_run_iteration_range(h, seed, iteration, first_packet, n_packets, n_total, t_inner):
+    return _check(load().mc_run_iteration_range(h, seed, iteration, first_packet, n_packets, n_total,
+                                                float(t_inner)), h)
 
 
 def mc_update_radiation_field(h, t_rad_out=None, w_out=None):
@@ -350,6 +358,10 @@ class Model:
 
     def run_iteration(self, seed, iteration, n_packets, t_inner):
         return mc_run_iteration(self.h, int(seed), int(iteration), int(n_packets), float(t_inner))
+
+    def run_iteration_range(self, seed, iteration, first, n_packets, n_total, t_inner):
+        return mc_run_iteration_range(self.h, int(seed), int(iteration), int(first), int(n_packets),
+                                      int(n_total), float(t_inner))
 
     def update_radiation_field(self):
         t, w = np.zeros(self.S), np.zeros(self.S)

@@ -2,10 +2,14 @@
 
     python -m paper_1401_5469_gb300.run_model [--model downbranch|scatter]
         [--lines L] [--packets N] [--iterations K] [--precision fp64|mixed]
+        [--first F --count C]
 
 Each iteration recomputes the Sobolev depths from T_R and W (downbranch
-model), transports the packets and updates T_R and W (Sect. 2.8).  Prints one
-line of totals and kernel times per iteration.  Used for profiling captures.
+model), transports the packets and updates T_R and W (Sect. 2.8).  With
+--first/--count only packets [F, F+C) of the N-packet iteration are
+transported (the draws of a packet depend only on its id), e.g. a single long
+random walk.  Prints one JSON line of totals and kernel times per iteration.
+Used for profiling captures.
 """
 from __future__ import annotations
 
@@ -23,6 +27,9 @@ def main():
     ap.add_argument("--iterations", type=int, default=2)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--seed", type=int, default=5469)
+    ap.add_argument("--first", type=int, default=0)
+    ap.add_argument("--count", type=int, default=None)
+    ap.add_argument("--update", type=int, default=1, help="update T_R, W between iterations")
     a = ap.parse_args()
     if a.model == "downbranch":
         kw = {}
@@ -39,15 +46,19 @@ def main():
         m.set_plasma(tau=spec.tau)
     else:
         m.set_plasma()
+    n = spec.n_packets
+    count = a.count if a.count is not None else n - a.first
     for it in range(a.iterations):
-        m.run_iteration(a.seed, it, spec.n_packets, spec.t_inner)
-        if spec.tau is None:
+        m.run_iteration_range(a.seed, it, a.first, count, n, spec.t_inner)
+        if spec.tau is None and a.update:
             m.update_radiation_field()
         _, st, _ = m.spectrum()
         ms = m.timing()
         ph = m.phases()
+        us = float(ms[1]) * 1e3 / max(st["segments"], 1)
         print(json.dumps({"iteration": it, "ms": [float(x) for x in ms],
-                          "bulk_ms": float(ph[0]), "tail_ms": float(ph[1]), **st}), flush=True)
+                          "bulk_ms": float(ph[0]), "tail_ms": float(ph[1]),
+                          "us_per_segment": us, **st}), flush=True)
     m.close()
 
 
