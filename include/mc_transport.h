@@ -239,6 +239,37 @@ mc_status mc_synchronize(mc_model *m);
 void mc_model_destroy(mc_model *m);
 
 /* ---------------------------------------------------------------------------
+ * Batched iterations of many models.
+ *
+ * A batch advances several mixed-precision models (MC_PRECISION_MIXED, one
+ * device, the same line mode, J_blue and record settings) by one
+ * Monte Carlo iteration each with a single persistent transport launch: the
+ * packets of all models are drawn from one queue, largest model first.  Each
+ * model's iteration is exactly its single-model iteration (same draws, same
+ * arithmetic; only the estimator summation order differs).  The whole
+ * iteration -- Sobolev depths where stale, estimator zeroing, transport and,
+ * when `update` is set, Eqs. 15-16 for every model -- is captured as one CUDA
+ * graph on the first call and replayed while the batch's shape (models with
+ * stale depths, update flag, total packets) is unchanged.  Results are read
+ * per model with mc_read_estimators / mc_read_spectrum / mc_read_plasma /
+ * mc_read_packets (ordered after the batch on the models' stream).  A model in
+ * a batch cannot be run alone until the batch is destroyed.
+ *  seeds, n_packets, t_inner: [n_models] in the order passed to
+ *  mc_batch_create.  Errors: MC_ERR_INVALID_ARG, MC_ERR_UNSUPPORTED (a model
+ *  not in mixed precision), MC_ERR_NOT_READY (no plasma state), MC_ERR_CUDA;
+ *  messages via mc_batch_last_error_message. */
+typedef struct mc_batch mc_batch;
+
+mc_status mc_batch_create(mc_model *const *models, uint32_t n_models, mc_batch **out);
+mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, uint32_t iteration,
+                                 const uint64_t *n_packets, const double *t_inner, int32_t update);
+mc_status mc_batch_synchronize(mc_batch *b);
+/* Device time of the last batched transport launch, ms[0] (synchronises). */
+mc_status mc_batch_read_timing(mc_batch *b, float *ms);
+const char *mc_batch_last_error_message(const mc_batch *b);
+void mc_batch_destroy(mc_batch *b);
+
+/* ---------------------------------------------------------------------------
  * Transport without any allocation.
  *
  * The paper has no counterpart to this entry point; it exists for callers that

@@ -1,0 +1,276 @@
+// Batched Monte Carlo iterations: many ejecta models of uneven size advanced
+// by one persistent transport launch per iteration, the whole iteration
+// (Sobolev depths, estimator zeroing, transport, radiation-field update of
+// every model) replayed as one captured CUDA graph.
+//
+// Each model keeps its own device arrays; the batch owns only the per-model
+// transport parameter table, the packet prefix sums and a work counter.  The
+// models' results are read with the single-model mc_read_* calls.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/mc_transport.h"
+#include "mc_internal.h"
+#include "mc_model_internal.h"
+
+using namespace mcgpu;
+
+namespace mcgpu {
+void set_create_error(const std::string &msg);
+}
+
+struct mc_batch {
+  std::vector<mc_model *> models;  // in launch order (largest packet count first)
+  std::vector<uint32_t> order;     // launch position -> caller's index
+  cudaStream_t stream = nullptr;   // the batch's own stream (graph capture)
+  std::vector<cudaStream_t> user;  // the models' distinct streams
+  int line_mode = 0;
+  bool j_blue = false, record = false;
+  int grid = 0;
+  TransportParams *d_params = nullptr, *h_params = nullptr;  // device table, pinned host staging
+  unsigned long long *d_prefix = nullptr, *h_prefix = nullptr;
+  unsigned long long *d_counters = nullptr;  // work counter, flags (kNCounterSlots)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> graph_shape;    // per model: 1 if its Sobolev depths were recomputed
+  std::vector<uint32_t> graph_order;  // launch order captured in the graph
+  bool graph_update = false;
+  uint64_t graph_total = 0;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+  uint64_t launches = 0, graph_launches = 0;
+  std::string err;
+};
+
+namespace {
+
+mc_status bfail(mc_batch *b, mc_status code, const std::string &msg) {
+  if (b) b->err = msg;
+  else set_create_error(msg);
+  return code;
+}
+
+mc_status bcuda(mc_batch *b, cudaError_t e, const char *what) {
+  return bfail(b, MC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Enqueue one iteration of every model on the batch stream.
+mc_status enqueue_iteration(mc_batch *b, int update) {
+  for (mc_model *m : b->models) {
+    const mc_status rc = model_prepare(m, b->stream, false);
+    if (rc != MC_OK) return bfail(b, rc, m->err);
+  }
+  cudaError_t e = cudaMemsetAsync(b->d_counters, 0, kNCounterSlots * sizeof(unsigned long long), b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_params, b->h_params, b->models.size() * sizeof(TransportParams),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "batch staging");
+  TransportParams p{};
+  p.batch = b->d_params;
+  p.batch_prefix = b->d_prefix;
+  p.n_models = static_cast<int32_t>(b->models.size());
+  p.n_packets = b->h_prefix[b->models.size()];
+  p.work_counter = b->d_counters;
+  p.flags = b->d_counters + 1;
+  e = cudaEventRecordWithFlags(b->t0, b->stream, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = launch_transport_batch(p, b->line_mode, b->j_blue, b->record, b->grid, b->stream);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->t1, b->stream, cudaEventRecordExternal);
+  if (e != cudaSuccess) return bcuda(b, e, "batched transport");
+  b->launches += 1;
+  if (update) {
+    for (mc_model *m : b->models) {
+      const mc_status rc = model_update(m, b->stream, false);
+      if (rc != MC_OK) return bfail(b, rc, m->err);
+    }
+  }
+  return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mc_status mc_batch_create(mc_model *const *models, uint32_t n_models, mc_batch **out) {
+  if (!out) return bfail(nullptr, MC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!models || n_models == 0) return bfail(nullptr, MC_ERR_INVALID_ARG, "need at least one model");
+  if (n_models > 4096) return bfail(nullptr, MC_ERR_INVALID_ARG, "at most 4096 models per batch");
+  const mc_model *m0 = models[0];
+  for (uint32_t i = 0; i < n_models; ++i) {
+    const mc_model *m = models[i];
+    if (!m) return bfail(nullptr, MC_ERR_INVALID_ARG, "NULL model");
+    if (m->in_batch) return bfail(nullptr, MC_ERR_INVALID_ARG, "a model already belongs to a batch");
+    if (m->run.precision != MC_PRECISION_MIXED)
+      return bfail(nullptr, MC_ERR_UNSUPPORTED, "batched launches use mixed-precision models");
+    if (m->device != m0->device || m->run.line_mode != m0->run.line_mode ||
+        (m->j_blue != nullptr) != (m0->j_blue != nullptr) || m->run.record_packets != m0->run.record_packets)
+      return bfail(nullptr, MC_ERR_INVALID_ARG, "batched models need one device, line mode, J_blue and record setting");
+    for (uint32_t k = 0; k < i; ++k)
+      if (models[k] == m) return bfail(nullptr, MC_ERR_INVALID_ARG, "a model appears twice");
+  }
+  mc_batch *b = new (std::nothrow) mc_batch();
+  if (!b) return bfail(nullptr, MC_ERR_OOM, "host allocation failed");
+  for (uint32_t i = 0; i < n_models; ++i)
+    if (std::find(b->user.begin(), b->user.end(), models[i]->stream) == b->user.end())
+      b->user.push_back(models[i]->stream);
+  b->line_mode = m0->run.line_mode;
+  b->j_blue = m0->j_blue != nullptr;
+  b->record = m0->run.record_packets != 0;
+  b->order.resize(n_models);
+  std::iota(b->order.begin(), b->order.end(), 0u);
+  for (uint32_t i = 0; i < n_models; ++i) b->models.push_back(models[i]);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_params, n_models * sizeof(TransportParams));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_prefix, (n_models + 1) * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, kNCounterSlots * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_params, n_models * sizeof(TransportParams));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_prefix, (n_models + 1) * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->t1);
+  int bps = 0, nsm = 1;
+  if (e == cudaSuccess) e = batch_occupancy(b->line_mode, b->j_blue, b->record, static_cast<int>(n_models), &bps);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m0->device);
+  if (e != cudaSuccess || bps <= 0) {
+    mc_batch_destroy(b);
+    return bfail(nullptr, MC_ERR_CUDA, std::string("batch create: ") + cudaGetErrorString(e));
+  }
+  b->grid = nsm * bps;
+  for (mc_model *m : b->models) m->in_batch = true;
+  *out = b;
+  return MC_OK;
+}
+
+mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, uint32_t iteration,
+                                 const uint64_t *n_packets, const double *t_inner, int32_t update) {
+  if (!b || !seeds || !n_packets || !t_inner) return MC_ERR_INVALID_ARG;
+  const size_t n = b->models.size();
+  // the previous iteration's graph reads the pinned parameter table when it
+  // starts; wait until it has been copied before overwriting it
+  if (b->graph_launches) {
+    const cudaError_t ew = cudaEventSynchronize(b->t0);
+    if (ew != cudaSuccess) return bcuda(b, ew, "previous iteration");
+  }
+  // launch order: largest packet count first, so the longest walks start first
+  std::vector<uint32_t> order(n);
+  std::iota(order.begin(), order.end(), 0u);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](uint32_t a, uint32_t c) { return n_packets[a] > n_packets[c]; });
+  std::vector<mc_model *> launch_models(n);
+  for (size_t k = 0; k < n; ++k) {
+    const uint32_t i = order[k];
+    mc_model *m = b->models[std::find(b->order.begin(), b->order.end(), i) - b->order.begin()];
+    launch_models[k] = m;
+    if (!m->plasma_set) return bfail(b, MC_ERR_NOT_READY, "a model has no plasma state");
+    if (n_packets[i] == 0 || n_packets[i] >= (1ull << 32))
+      return bfail(b, MC_ERR_INVALID_ARG, "need 0 < n_packets < 2^32 for every model");
+    if (m->run.record_packets && n_packets[i] > m->run.max_packets)
+      return bfail(b, MC_ERR_INVALID_ARG, "n_packets exceeds a model's packet records");
+    if (!(t_inner[i] > 0.0) || !std::isfinite(t_inner[i])) return bfail(b, MC_ERR_INVALID_ARG, "t_inner must be positive");
+  }
+  b->models = launch_models;
+  b->order = order;
+  b->h_prefix[0] = 0;
+  std::vector<int> shape(n);
+  for (size_t k = 0; k < n; ++k) {
+    const uint32_t i = order[k];
+    mc_model *m = b->models[k];
+    model_fill_transport(m, b->h_params[k], seeds[i], iteration, 0, n_packets[i], n_packets[i], t_inner[i]);
+    b->h_prefix[k + 1] = b->h_prefix[k] + n_packets[i];
+    shape[k] = (!m->tau_given && m->tau_dirty) ? 1 : 0;
+  }
+  // the prefix table is constant across graph replays of the same shape
+  cudaError_t e = cudaMemcpyAsync(b->d_prefix, b->h_prefix, (n + 1) * sizeof(unsigned long long),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "prefix upload");
+  // order the batch after the models' own stream
+  for (cudaStream_t us : b->user) {
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_in, us);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_in, 0);
+  }
+  if (e != cudaSuccess) return bcuda(b, e, "stream order");
+
+  const bool reuse = b->exec && b->graph_shape == shape && b->graph_order == order &&
+                     b->graph_update == (update != 0) &&
+                     b->graph_total == b->h_prefix[n];
+  if (!reuse) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(b, e, "begin capture");
+    const mc_status rc = enqueue_iteration(b, update);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->stream, &g);
+    if (rc != MC_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return bcuda(b, e, "end capture");
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
+    b->graph_shape = shape;
+    b->graph_order = order;
+    b->graph_update = update != 0;
+    b->graph_total = b->h_prefix[n];
+  } else {
+    // the captured steps mark the same state; keep the host-side flags in step
+    for (mc_model *m : b->models) {
+      m->ran_plasma = false;
+      if (!m->tau_given && m->tau_dirty) m->tau_dirty = false;
+    }
+  }
+  e = cudaGraphLaunch(b->exec, b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "graph launch");
+  b->graph_launches += 1;
+  for (size_t k = 0; k < n; ++k) {
+    mc_model *m = b->models[k];
+    m->have_run = true;
+    m->last_n = n_packets[order[k]];
+    if (update && !m->tau_given) m->tau_dirty = true;
+  }
+  e = cudaEventRecord(b->ev_out, b->stream);
+  for (cudaStream_t us : b->user)
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(us, b->ev_out, 0);
+  if (e != cudaSuccess) return bcuda(b, e, "stream order");
+  return MC_OK;
+}
+
+mc_status mc_batch_synchronize(mc_batch *b) {
+  if (!b) return MC_ERR_INVALID_ARG;
+  const cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "batch synchronize");
+  return MC_OK;
+}
+
+mc_status mc_batch_read_timing(mc_batch *b, float *ms) {
+  if (!b || !ms) return MC_ERR_INVALID_ARG;
+  if (!b->graph_launches) return bfail(b, MC_ERR_NOT_READY, "no batched iteration yet");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, b->t0, b->t1);
+  if (e != cudaSuccess) return bcuda(b, e, "batch timing");
+  return MC_OK;
+}
+
+const char *mc_batch_last_error_message(const mc_batch *b) { return b ? b->err.c_str() : ""; }
+
+void mc_batch_destroy(mc_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (mc_model *m : b->models) m->in_batch = false;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->d_params) cudaFree(b->d_params);
+  if (b->d_prefix) cudaFree(b->d_prefix);
+  if (b->d_counters) cudaFree(b->d_counters);
+  if (b->h_params) cudaFreeHost(b->h_params);
+  if (b->h_prefix) cudaFreeHost(b->h_prefix);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->t0) cudaEventDestroy(b->t0);
+  if (b->t1) cudaEventDestroy(b->t1);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // extern "C"

@@ -12,6 +12,7 @@
 
 #include "../../include/mc_transport.h"
 #include "mc_internal.h"
+#include "mc_model_internal.h"
 
 using namespace mcgpu;
 
@@ -19,56 +20,9 @@ namespace {
 
 thread_local std::string g_create_error;
 
-enum Ev { kEvPlasma0 = 0, kEvPlasma1, kEvTransport0, kEvTransport1, kEvUpdate0, kEvUpdate1, kNEv };
 
 }  // namespace
 
-struct mc_model {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  mc_allocator alloc{};
-  bool has_alloc = false;
-  std::vector<void *> allocations;
-  std::string err;
-
-  uint32_t S = 0, L = 0, I = 0, K = 0;
-  uint64_t nnz = 0;
-  mc_run_desc run{};
-  double t_exp = 0.0;
-  bool has_atomic = false, has_line_meta = false;
-
-  double *x_in = nullptr, *x_out = nullptr, *inv_x_in = nullptr, *inv_x_out = nullptr;
-  double *kappa = nullptr, *inv_kappa = nullptr;
-  DbrRec *dbr_rec = nullptr, *dbr_bucket = nullptr;
-  unsigned long long *row_info = nullptr;
-  float *kappa32 = nullptr, *x_in32 = nullptr, *x_out32 = nullptr;
-  double *nu = nullptr, *tau = nullptr;
-  float *tau32 = nullptr;
-  int32_t *line_row = nullptr, *lev_l = nullptr, *lev_u = nullptr;
-  double *line_pref = nullptr, *line_gratio = nullptr;
-  uint32_t *dbr_offset = nullptr, *dbr_line = nullptr;
-  double *dbr_cdf = nullptr;
-  double *t_rad = nullptr, *w = nullptr, *eps_erg = nullptr, *g = nullptr, *n_ion = nullptr,
-         *pop = nullptr;
-  uint8_t *meta = nullptr;
-  double *norm = nullptr;
-  double *j_est = nullptr, *nu_bar = nullptr, *j_blue = nullptr, *spectrum = nullptr;
-  unsigned long long *counters = nullptr;  // stats [kNStats], work counter, flags
-  double *planck_cdf = nullptr;
-  int32_t *rec_status = nullptr;
-  double *rec_nu = nullptr, *rec_e = nullptr;
-  unsigned long long *rec_cnt = nullptr;
-
-  std::vector<double> host_norm, host_x_in, host_x_out;
-  double r_inner = 0.0;
-  bool plasma_set = false, tau_given = false, tau_dirty = true, have_run = false;
-  bool ran_plasma = false, ran_update = false;
-  uint64_t last_n = 0;
-  cudaEvent_t ev[kNEv] = {};
-  uint64_t launches = 0;
-  int grid = 0;
-};
 
 namespace {
 
@@ -314,6 +268,7 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
             alloc_n(m, &m->counters, static_cast<size_t>(kNCounterSlots)) &&
             alloc_n(m, &m->planck_cdf, static_cast<size_t>(kPlanckLmax) + 1);
   if (ok && run->j_blue) ok = alloc_n(m, &m->j_blue, SL);
+  if (ok && run->precision == MC_PRECISION_MIXED) ok = alloc_n(m, &m->shell32, 4 * static_cast<size_t>(S));
   if (ok && meta) ok = alloc_n(m, &m->line_row, L) && alloc_n(m, &m->lev_l, L) && alloc_n(m, &m->lev_u, L);
   if (ok && atomic) {
     const size_t IK = static_cast<size_t>(I) * K;
@@ -370,6 +325,18 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
   chk(upload(m, m->inv_x_out, ixo.data(), S));
   chk(upload(m, m->kappa, kap.data(), S));
   chk(upload(m, m->inv_kappa, ikap.data(), S));
+  std::vector<float> sh32;
+  if (m->shell32) {
+    sh32.resize(4 * static_cast<size_t>(S));
+    for (uint32_t s = 0; s < S; ++s) {
+      const float fi = static_cast<float>(xi[s]), fo = static_cast<float>(xo[s]);
+      sh32[s] = fi * fi;
+      sh32[S + s] = fo * fo;
+      sh32[2 * S + s] = static_cast<float>(kap[s]);
+      sh32[3 * S + s] = kap[s] > 0.0 ? static_cast<float>(1.0 / kap[s]) : 0.0f;
+    }
+    chk(upload(m, m->shell32, sh32.data(), sh32.size()));
+  }
   chk(upload(m, m->norm, norm.data(), S));
   chk(upload(m, m->nu, lines->nu, L));
   chk(upload(m, m->planck_cdf, cdf.data(), cdf.size()));
@@ -494,25 +461,56 @@ mc_status mc_run_iteration_range(mc_model *m, uint64_t seed, uint32_t iteration,
   if (m->run.record_packets && n_packets > m->run.max_packets)
     return fail(m, MC_ERR_INVALID_ARG, "n_packets exceeds max_packets of the packet records");
   if (!(t_inner > 0.0) || !std::isfinite(t_inner)) return fail(m, MC_ERR_INVALID_ARG, "t_inner must be positive");
-  cudaError_t e;
+  if (m->in_batch) return fail(m, MC_ERR_INVALID_ARG, "the model belongs to a batch; run it through the batch");
+  mc_status st = model_prepare(m, m->stream, true);
+  if (st != MC_OK) return st;
+  TransportParams p{};
+  model_fill_transport(m, p, seed, iteration, first_packet, n_packets, n_total, t_inner);
+  cudaEventRecord(m->ev[kEvTransport0], m->stream);
+  cudaError_t e = launch_transport(p, m->run.line_mode, m->run.precision, m->j_blue != nullptr,
+                                   m->run.record_packets != 0, m->grid, transport_block_size(), m->stream);
+  if (e != cudaSuccess) return cuda_fail(m, e, "transport kernel");
+  cudaEventRecord(m->ev[kEvTransport1], m->stream);
+  m->launches += 1;
+  m->have_run = true;
+  m->ran_update = false;
+  m->last_n = n_packets;
+  return MC_OK;
+}
+
+}  // extern "C"
+
+namespace mcgpu {
+
+mc_status model_fail(mc_model *m, mc_status code, const std::string &msg) { return fail(m, code, msg); }
+
+mc_status model_prepare(mc_model *m, cudaStream_t st, bool events) {
   m->ran_plasma = false;
   if (!m->tau_given && m->tau_dirty) {
-    cudaEventRecord(m->ev[kEvPlasma0], m->stream);
-    mc_status st = recompute_tau(m);
-    if (st != MC_OK) return st;
-    cudaEventRecord(m->ev[kEvPlasma1], m->stream);
-    m->ran_plasma = true;
+    if (events) cudaEventRecord(m->ev[kEvPlasma0], st);
+    cudaStream_t own = m->stream;
+    m->stream = st;
+    const mc_status rc = recompute_tau(m);
+    m->stream = own;
+    if (rc != MC_OK) return rc;
+    if (events) cudaEventRecord(m->ev[kEvPlasma1], st);
+    m->ran_plasma = events;
   }
-  e = launch_zero(m->j_est, m->S, m->nu_bar, m->S, m->spectrum, m->run.spec_bins + 2, m->counters,
-                  kNCounterSlots, m->stream);
+  cudaError_t e = launch_zero(m->j_est, m->S, m->nu_bar, m->S, m->spectrum, m->run.spec_bins + 2,
+                              m->counters, kNCounterSlots, st);
   if (e != cudaSuccess) return cuda_fail(m, e, "zero");
   m->launches += 1;
   if (m->j_blue) {
-    e = launch_zero_large(m->j_blue, static_cast<size_t>(m->S) * m->L, m->stream);
+    e = launch_zero_large(m->j_blue, static_cast<size_t>(m->S) * m->L, st);
     if (e != cudaSuccess) return cuda_fail(m, e, "zero j_blue");
     m->launches += 1;
   }
-  TransportParams p{};
+  return MC_OK;
+}
+
+void model_fill_transport(const mc_model *m, TransportParams &p, uint64_t seed, uint32_t iteration,
+                          uint64_t first_packet, uint64_t n_packets, uint64_t n_total, double t_inner) {
+  p = TransportParams{};
   p.S = static_cast<int32_t>(m->S);
   p.L = static_cast<int32_t>(m->L);
   p.x_in = m->x_in; p.x_out = m->x_out; p.inv_x_in = m->inv_x_in; p.inv_x_out = m->inv_x_out;
@@ -543,33 +541,35 @@ mc_status mc_run_iteration_range(mc_model *m, uint64_t seed, uint32_t iteration,
   p.max_segments = m->run.max_segments;
   p.rec_status = m->rec_status; p.rec_nu = m->rec_nu; p.rec_e = m->rec_e; p.rec_cnt = m->rec_cnt;
   p.timeout_ns = m->run.timeout_ns;
-  cudaEventRecord(m->ev[kEvTransport0], m->stream);
-  e = launch_transport(p, m->run.line_mode, m->run.precision, m->j_blue != nullptr,
-                       m->run.record_packets != 0, m->grid, transport_block_size(), m->stream);
-  if (e != cudaSuccess) return cuda_fail(m, e, "transport kernel");
-  cudaEventRecord(m->ev[kEvTransport1], m->stream);
-  m->launches += 1;
-  m->have_run = true;
-  m->ran_update = false;
-  m->last_n = n_packets;
-  return MC_OK;
+  p.shell32 = m->shell32;
 }
 
-mc_status mc_update_radiation_field(mc_model *m, double *t_rad_out, double *w_out) {
-  if (!m) return MC_ERR_INVALID_ARG;
-  if (!m->have_run) return fail(m, MC_ERR_NOT_READY, "no Monte Carlo run to update from");
+mc_status model_update(mc_model *m, cudaStream_t st, bool events) {
   UpdateParams u{};
   u.S = static_cast<int32_t>(m->S);
   u.j_est = m->j_est; u.nu_bar = m->nu_bar; u.norm = m->norm;
   u.t_rad = m->t_rad; u.w = m->w;
   u.c_tr = (kH / kKB) * ((kPi * kPi * kPi * kPi) / (360.0 * kZeta5));
-  cudaEventRecord(m->ev[kEvUpdate0], m->stream);
-  cudaError_t e = launch_update(u, m->stream);
+  if (events) cudaEventRecord(m->ev[kEvUpdate0], st);
+  cudaError_t e = launch_update(u, st);
   if (e != cudaSuccess) return cuda_fail(m, e, "update kernel");
-  cudaEventRecord(m->ev[kEvUpdate1], m->stream);
+  if (events) cudaEventRecord(m->ev[kEvUpdate1], st);
   m->launches += 1;
-  m->ran_update = true;
+  m->ran_update = events;
   if (!m->tau_given) m->tau_dirty = true;
+  return MC_OK;
+}
+
+}  // namespace mcgpu
+
+extern "C" {
+
+mc_status mc_update_radiation_field(mc_model *m, double *t_rad_out, double *w_out) {
+  if (!m) return MC_ERR_INVALID_ARG;
+  if (!m->have_run) return fail(m, MC_ERR_NOT_READY, "no Monte Carlo run to update from");
+  mc_status st = model_update(m, m->stream, true);
+  if (st != MC_OK) return st;
+  cudaError_t e = cudaSuccess;
   if (t_rad_out) e = cudaMemcpyAsync(t_rad_out, m->t_rad, m->S * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess && w_out) e = cudaMemcpyAsync(w_out, m->w, m->S * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);

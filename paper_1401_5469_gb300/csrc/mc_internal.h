@@ -77,6 +77,10 @@ struct TransportParams {
   int32_t *rec_status;               // per-packet records or nullptrs
   double *rec_nu, *rec_e;
   unsigned long long *rec_cnt;       // [n * kNCounters]
+  const float *shell32;              // [4 S] binary32 shell table (mixed; batched launch)
+  const TransportParams *batch;      // batched launch: per-model parameters, or nullptr
+  const unsigned long long *batch_prefix;  // [n_models + 1] packet offsets of the models
+  int32_t n_models;
   unsigned long long timeout_ns;     // 0 = none
   unsigned long long *flags;         // [0] deadline hit, [1] work queue empty (ns),
                                      // [2] last warp done (ns), [3] first warp start (ns)
@@ -114,6 +118,9 @@ int transport_block_size();
 cudaError_t transport_occupancy(int line_mode, int precision, bool j_blue, bool record, int S,
                                 int *blocks_per_sm);
 const void *select_mixed_kernel(int line_mode, bool j_blue, bool record);
+cudaError_t batch_occupancy(int line_mode, bool j_blue, bool record, int n_models, int *blocks_per_sm);
+cudaError_t launch_transport_batch(const TransportParams &p, int line_mode, bool j_blue, bool record,
+                                   int grid, cudaStream_t st);
 size_t mixed_smem_bytes(int S);
 cudaError_t launch_to_f32(const double *in, float *out, size_t n, cudaStream_t st);
 cudaError_t launch_populations(const PlasmaParams &p, cudaStream_t st);

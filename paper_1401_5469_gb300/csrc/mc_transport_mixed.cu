@@ -1,15 +1,23 @@
 // Mixed-precision Monte Carlo packet transport (same method as
-// mc_transport.cu, Kerzendorf & Sim 2014 Sects. 2.4-2.7, 2.9).
+// mc_transport.cu, Kerzendorf & Sim 2014 Sects. 2.4-2.7, 2.9), for one model
+// or for a batch of models in one persistent launch.
 //
 // Precision split.  Geometry (x mu, impact parameter, radius), path lengths,
-// optical depths, the logarithm of the event draw, packet energy and the
-// frame factors are binary32.  Binary64 is kept where the method needs it:
-// the lab and comoving frequencies, the Sobolev-resonance comparison against
-// the frequency-sorted line list (integer keys of binary64 values), the
-// frequency thresholds that the optical depth is accumulated into, and the
-// estimator sums.  The lab frequency after a re-emission is nu_c / D to
-// binary64 accuracy (Newton step on the binary32 reciprocal), so the comoving
-// frequency at the emission point is the emitting line's frequency.
+// optical depths, the logarithm of the event draw, packet energies (relative
+// to the injection energy) and the frame factors are binary32.  Binary64 is
+// kept where the method needs it: the lab and comoving frequencies, the
+// Sobolev-resonance comparison against the frequency-sorted line list
+// (integer keys of binary64 values), the frequency thresholds that the optical
+// depth is accumulated into, and the estimator sums.  The lab frequency after
+// a re-emission is nu_c / D to binary64 accuracy (Newton step on the binary32
+// reciprocal), so the comoving frequency at the emission point is the emitting
+// line's frequency.
+//
+// Batched launch.  Packets of all models are claimed from one queue (models
+// laid out by a prefix sum of their packet counts, largest first so that the
+// longest random walks start first); a lane that claims a packet of another
+// model loads that model's context and first flushes its register
+// accumulators to the previous model.
 #include <cstdint>
 
 #include "mc_device.cuh"
@@ -20,18 +28,73 @@ namespace mcgpu {
 namespace {
 
 constexpr int kBlock = 128;
-constexpr int kShellArrays = 4;  // x_in^2, x_out^2, kappa, 1/kappa (binary32)
 constexpr int kLineEvent = 1, kElectronEvent = 2, kShellEvent = 3;
 
 struct PacketM {
-  double nu_lab;             // binary64
-  float p, q, r2;            // x mu, x^2 - p^2, x^2
-  float e_lab, inv_nu, inv_D;
+  double nu_lab;               // binary64
+  float p, q, r2;              // x mu, x^2 - p^2, x^2
+  float e_lab, inv_nu, inv_D;  // e_lab relative to the injection energy
   int32_t shell, next_line;
   uint32_t pid;
   bool have_inv_D;
   uint32_t cnt[kNCounters];
 };
+
+// What a lane needs of its packet's model.
+struct MCtx {
+  const float *xi2, *xo2, *kap, *ikap;
+  const double *nu;
+  const float *tau32;
+  const unsigned long long *row_info;
+  const DbrRec *bucket, *rec;
+  double *j_blue, *j_est, *nu_bar, *spectrum;
+  unsigned long long *stats;
+  const double *planck;
+  int32_t S, L, spec_bins;
+  uint32_t key0, key1, iteration;
+  double spec_lo, spec_dnu, e_cmf, nu_scale;
+  uint64_t max_segments, first_packet;
+  float x0, x0sq;
+  int32_t *rec_status;
+  double *rec_nu, *rec_e;
+  unsigned long long *rec_cnt;
+};
+
+__device__ __forceinline__ void load_ctx(MCtx &c, const TransportParams &q, const float *shell) {
+  c.S = q.S;
+  c.L = q.L;
+  c.xi2 = shell;
+  c.xo2 = shell + q.S;
+  c.kap = shell + 2 * q.S;
+  c.ikap = shell + 3 * q.S;
+  c.nu = q.nu;
+  c.tau32 = q.tau32;
+  c.row_info = q.row_info;
+  c.bucket = q.dbr_bucket;
+  c.rec = q.dbr_rec;
+  c.j_blue = q.j_blue;
+  c.j_est = q.j_est;
+  c.nu_bar = q.nu_bar;
+  c.spectrum = q.spectrum;
+  c.stats = q.stats;
+  c.planck = q.planck_cdf;
+  c.spec_bins = q.spec_bins;
+  c.key0 = q.key0;
+  c.key1 = q.key1;
+  c.iteration = q.iteration;
+  c.spec_lo = q.spec_lo;
+  c.spec_dnu = q.spec_dnu;
+  c.e_cmf = q.e_cmf;
+  c.nu_scale = q.nu_scale;
+  c.max_segments = q.max_segments;
+  c.first_packet = q.first_packet;
+  c.x0 = static_cast<float>(q.x_in[0]);
+  c.x0sq = shell[0];
+  c.rec_status = q.rec_status;
+  c.rec_nu = q.rec_nu;
+  c.rec_e = q.rec_e;
+  c.rec_cnt = q.rec_cnt;
+}
 
 __device__ __forceinline__ int32_t first_redward_m(const double *nu, int32_t L, double v) {
   const long long kv = __double_as_longlong(v);
@@ -45,11 +108,11 @@ __device__ __forceinline__ int32_t first_redward_m(const double *nu, int32_t L, 
 }
 
 // Same exact integer search as the binary64 kernel (downbranch emission).
-__device__ __forceinline__ void pick_m(const TransportParams &p, unsigned long long rinfo,
-                                       unsigned long long u, double &nu, float &inv_nu, int32_t &line) {
+__device__ __forceinline__ void pick_m(const MCtx &c, unsigned long long rinfo, unsigned long long u,
+                                       double &nu, float &inv_nu, int32_t &line) {
   const uint32_t b = static_cast<uint32_t>(rinfo), len = static_cast<uint32_t>(rinfo >> 32);
   const uint32_t bucket = static_cast<uint32_t>(__umul64hi(u << 11, static_cast<unsigned long long>(len)));
-  const DbrRec *slot = p.dbr_bucket + b + bucket;
+  const DbrRec *slot = c.bucket + b + bucket;
   unsigned long long thr = __ldg(&slot->thr);
   if (u < thr) {
     nu = __ldg(&slot->nu);
@@ -57,7 +120,7 @@ __device__ __forceinline__ void pick_m(const TransportParams &p, unsigned long l
     line = static_cast<int32_t>(__ldg(&slot->emit));
     return;
   }
-  const DbrRec *rec = p.dbr_rec;
+  const DbrRec *rec = c.rec;
   uint32_t i = b + __ldg(&slot->guide) + 1u;
   thr = __ldg(&rec[i].thr);
   while (u >= thr) { ++i; thr = __ldg(&rec[i].thr); }
@@ -68,42 +131,52 @@ __device__ __forceinline__ void pick_m(const TransportParams &p, unsigned long l
 
 __device__ __forceinline__ float max0f(float v) { return v > 0.0f ? v : 0.0f; }
 
-// uniform in (0, 1] / [0, 1) with 24 random bits
+// uniform in (0, 1] with 24 random bits
 __device__ __forceinline__ float open0f(unsigned long long u53) {
   return static_cast<float>((u53 >> 29) + 1ull) * 0x1.0p-24f;
 }
 
-template <int MODE, bool JB, bool REC>
-__global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams p) {
-  extern __shared__ float shf[];
-  const int32_t S = p.S, L = p.L;
-  for (int i = threadIdx.x; i < S; i += blockDim.x) {
-    const float xi = static_cast<float>(p.x_in[i]), xo = static_cast<float>(p.x_out[i]);
-    const double kap = p.kappa[i];
-    shf[i] = xi * xi;
-    shf[S + i] = xo * xo;
-    shf[2 * S + i] = static_cast<float>(kap);
-    shf[3 * S + i] = kap > 0.0 ? static_cast<float>(1.0 / kap) : 0.0f;
-  }
-  __syncthreads();
-  const float *s_xi2 = shf, *s_xo2 = shf + S, *s_kap = shf + 2 * S, *s_ikap = shf + 3 * S;
-  const double x0d = p.x_in[0];
-  const float x0 = static_cast<float>(x0d), x0sq = s_xi2[0];
+struct Stats {
+  unsigned long long v[kNStats];
+};
 
+__device__ __forceinline__ void flush_stats(Stats &st, unsigned long long *dst) {
+#pragma unroll
+  for (int i = 0; i < kNStats; ++i) {
+    if (st.v[i]) atomicAdd(dst + i, st.v[i]);
+    st.v[i] = 0ull;
+  }
+}
+
+template <int MODE, bool JB, bool REC, bool BATCH>
+__global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams p) {
+  extern __shared__ unsigned long long smem_u64[];
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lanemask_lt = (1u << lane) - 1u;
+  MCtx c;
+  int32_t cur_model = -1;
+  unsigned long long *prefix = smem_u64;
+  if (BATCH) {
+    for (int i = threadIdx.x; i <= p.n_models; i += blockDim.x) prefix[i] = p.batch_prefix[i];
+    __syncthreads();
+  } else {
+    float *shf = reinterpret_cast<float *>(smem_u64);
+    for (int i = threadIdx.x; i < 4 * p.S; i += blockDim.x) shf[i] = p.shell32[i];
+    __syncthreads();
+    load_ctx(c, p, shf);
+    cur_model = 0;
+  }
   const unsigned long long t_start = global_ns();
   if (lane == 0u) atomicCAS(p.flags + 3, 0ull, t_start);
 
   PacketM pk;
   DrawStream ds;
   bool alive = false, finished = false;
-  unsigned long long n_esc = 0, n_reab = 0, n_cap = 0, n_seg = 0, n_chk = 0, n_res = 0, n_lint = 0,
-                     n_esca = 0, n_shell = 0;
+  Stats st;
+#pragma unroll
+  for (int i = 0; i < kNStats; ++i) st.v[i] = 0ull;
   int32_t acc_s = -1;
   double acc_j = 0.0, acc_nb = 0.0;
-  const long long *nub = reinterpret_cast<const long long *>(p.nu);
-  const double e_cmf0 = p.e_cmf;  // binary32 energies are carried relative to this
 
   for (;;) {
     const bool need = !alive && !finished;
@@ -115,34 +188,54 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         base = atomicAdd(p.work_counter, static_cast<unsigned long long>(__popc(needmask)));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
-        const unsigned long long id = base + __popc(needmask & lanemask_lt);
+        unsigned long long id = base + __popc(needmask & lanemask_lt);
         if (id < p.n_packets) {
+          if (BATCH) {
+            int lo = 0, hi = p.n_models;  // model m with prefix[m] <= id < prefix[m+1]
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (prefix[mid] <= id) lo = mid; else hi = mid;
+            }
+            if (lo != cur_model) {
+              if (cur_model >= 0) {
+                if (acc_s >= 0) {
+                  atomicAdd(c.j_est + acc_s, acc_j * c.e_cmf);
+                  atomicAdd(c.nu_bar + acc_s, acc_nb * c.e_cmf);
+                }
+                flush_stats(st, c.stats);
+              }
+              acc_s = -1; acc_j = 0.0; acc_nb = 0.0;
+              load_ctx(c, p.batch[lo], p.batch[lo].shell32);
+              cur_model = lo;
+            }
+            id -= prefix[lo];
+          }
           // injection (Sect. 2.4), same draws as the binary64 kernel
-          pk.pid = static_cast<uint32_t>(p.first_packet + id);
-          ds.init(p.key0, p.key1, pk.pid, p.iteration);
+          pk.pid = static_cast<uint32_t>(c.first_packet + id);
+          ds.init(c.key0, c.key1, pk.pid, c.iteration);
           const double z0 = ds.closed0();
           const double z1 = ds.open0(), z2 = ds.open0(), z3 = ds.open0(), z4 = ds.open0();
           int l = 1;
-          while (l < kPlanckLmax && p.planck_cdf[l] < z0) ++l;
+          while (l < kPlanckLmax && c.planck[l] < z0) ++l;
           double xi = -log_pos(((z1 * z2) * z3) * z4);
           if (l > 1) xi = xi / static_cast<double>(l);
-          const double nu_cmf = p.nu_scale * xi;
+          const double nu_cmf = c.nu_scale * xi;
           const float mu = sqrtf(open0f(ds.next_u53()));
-          const float pp = x0 * mu;
+          const float pp = c.x0 * mu;
           const float D = 1.0f - pp;
           const float iD = 1.0f / D;
           pk.p = pp;
-          pk.r2 = x0sq;
-          pk.q = max0f(fmaf(-pp, pp, x0sq));
+          pk.r2 = c.x0sq;
+          pk.q = max0f(fmaf(-pp, pp, c.x0sq));
           pk.nu_lab = nu_cmf * static_cast<double>(iD);
           pk.e_lab = iD;  // E_lab / E_cmf(injection)
           pk.inv_nu = static_cast<float>(1.0 / nu_cmf) * D;
           pk.inv_D = iD;
           pk.have_inv_D = true;
           pk.shell = 0;
-          pk.next_line = first_redward_m(p.nu, L, nu_cmf);
+          pk.next_line = first_redward_m(c.nu, c.L, nu_cmf);
 #pragma unroll
-          for (int c = 0; c < kNCounters; ++c) pk.cnt[c] = 0u;
+          for (int k = 0; k < kNCounters; ++k) pk.cnt[k] = 0u;
           alive = true;
         } else {
           finished = true;
@@ -163,21 +256,22 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
     if (!alive) continue;
 
     int status = 0;
-    if (pk.cnt[0] >= p.max_segments) {
+    if (pk.cnt[0] >= c.max_segments) {
       status = 3;
     } else {
       pk.cnt[0] += 1u;
       const int32_t s = pk.shell;
+      const int32_t L = c.L;
       const float pp = pk.p, q = pk.q, r2 = pk.r2, inv_nu = pk.inv_nu;
       const double nu_lab = pk.nu_lab;
       const float Df = 1.0f - pp;
       const float inv_D = pk.have_inv_D ? pk.inv_D : 1.0f / Df;
       const double nu_cmf = nu_lab * static_cast<double>(Df);
       const float eD2 = (pk.e_lab * Df) * Df;
-      const float kap = s_kap[s];
+      const float kap = c.kap[s];
       const bool thomson = kap > 0.0f;
       const float tau0 = -__logf(open0f(ds.next_u53()));
-      const float xi2 = s_xi2[s], xo2 = s_xo2[s];
+      const float xi2 = c.xi2[s], xo2 = c.xo2[s];
       const bool inner = pp < 0.0f && q <= xi2;
       const float root = sqrtf(max0f((inner ? xi2 : xo2) - q));
       const float p_exit = inner ? -root : root;
@@ -186,14 +280,15 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
       double thr_e = 0.0;
       long long key_e = kKeyNegInf;
       if (thomson) {
-        c_e = (static_cast<float>(nu_lab) * s_ikap[s]) * inv_D;  // nu_lab / k
+        c_e = (static_cast<float>(nu_lab) * c.ikap[s]) * inv_D;  // nu_lab / k
         thr_e = nu_cmf - static_cast<double>(tau0 * c_e);
         key_e = okey(thr_e);
       }
       long long key_thr = key_shell > key_e ? key_shell : key_e;
       const float e_inv2 = JB ? (pk.e_lab * inv_nu) * inv_nu : 0.0f;
       const size_t row = static_cast<size_t>(s) * static_cast<size_t>(L);
-      const float *tau_s = p.tau32 + row;
+      const float *tau_s = c.tau32 + row;
+      const long long *nub = reinterpret_cast<const long long *>(c.nu);
       int32_t j = pk.next_line;
       int kind = 0;
       float l = 0.0f;
@@ -205,12 +300,12 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
       if (j < L) {
         bj = __ldg(nub + j);
         taul = __ldg(tau_s + j);
-        if (MODE == 1) rinfo = __ldg(p.row_info + j);
+        if (MODE == 1) rinfo = __ldg(c.row_info + j);
       }
       if (j + 1 < L) {
         bj_n = __ldg(nub + j + 1);
         tau_n = __ldg(tau_s + j + 1);
-        if (MODE == 1) rinfo_n = __ldg(p.row_info + j + 1);
+        if (MODE == 1) rinfo_n = __ldg(c.row_info + j + 1);
       }
       while (j < L) {
         pk.cnt[1] += 1u;
@@ -220,12 +315,12 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         if (j + 2 < L) {
           bj_nn = __ldg(nub + j + 2);
           tau_nn = __ldg(tau_s + j + 2);
-          if (MODE == 1) rinfo_nn = __ldg(p.row_info + j + 2);
+          if (MODE == 1) rinfo_nn = __ldg(c.row_info + j + 2);
         }
         if (bj <= key_thr) break;
         pk.cnt[2] += 1u;
         const double nuj = __longlong_as_double(bj);
-        if (JB) atomicAdd(p.j_blue + row + j, static_cast<double>(static_cast<float>(nuj) * e_inv2) * e_cmf0);
+        if (JB) atomicAdd(c.j_blue + row + j, static_cast<double>(static_cast<float>(nuj) * e_inv2) * c.e_cmf);
         bool absorbed;
         if (thomson) {
           const double t = thr_e + static_cast<double>(taul * c_e);
@@ -254,12 +349,12 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         if (key_e > key_shell) { kind = kElectronEvent; l = max0f(static_cast<float>(nu_cmf - thr_e) * inv_nu); }
         else { kind = kShellEvent; l = max0f(p_exit - pp); }
       }
-      // estimators (binary32 contribution, binary64 sums)
+      // estimators (binary32 contribution, binary64 sums in units of E)
       const double wgt = static_cast<double>(eD2 * l);
       if (s != acc_s) {
         if (acc_s >= 0) {
-          atomicAdd(p.j_est + acc_s, acc_j * e_cmf0);
-          atomicAdd(p.nu_bar + acc_s, acc_nb * e_cmf0);
+          atomicAdd(c.j_est + acc_s, acc_j * c.e_cmf);
+          atomicAdd(c.nu_bar + acc_s, acc_nb * c.e_cmf);
         }
         acc_s = s; acc_j = 0.0; acc_nb = 0.0;
       }
@@ -273,7 +368,7 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         pk.r2 = inner ? xi2 : xo2;
         pk.shell = ns;
         pk.have_inv_D = false;
-        if (ns >= S) status = 1;
+        if (ns >= c.S) status = 1;
         else if (ns < 0) status = 2;
       } else {
         const float pl = pp + l;
@@ -287,7 +382,7 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
           pk.cnt[3] += 1u;
           if (MODE == 1) {
             int32_t emit;
-            pick_m(p, rinfo_hit, ds.next_u53(), nu_c, inv_nu_c, emit);
+            pick_m(c, rinfo_hit, ds.next_u53(), nu_c, inv_nu_c, emit);
             pk.next_line = emit + 1;
           } else {
             nu_c = nu_hit;
@@ -318,68 +413,79 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
       }
     }
     if (status != 0) {
-      if (status == 1) ++n_esc;
-      else if (status == 2) ++n_reab;
-      else ++n_cap;
-      n_seg += pk.cnt[0];
-      n_chk += pk.cnt[1];
-      n_res += pk.cnt[2];
-      n_lint += pk.cnt[3];
-      n_esca += pk.cnt[4];
-      n_shell += pk.cnt[5];
-      const double e_lab = static_cast<double>(pk.e_lab) * e_cmf0;
+      if (status == 1) st.v[kStEscaped] += 1ull;
+      else if (status == 2) st.v[kStReabsorbed] += 1ull;
+      else st.v[kStCapped] += 1ull;
+      st.v[kStSegments] += pk.cnt[0];
+      st.v[kStLineChecks] += pk.cnt[1];
+      st.v[kStResonances] += pk.cnt[2];
+      st.v[kStLineInteractions] += pk.cnt[3];
+      st.v[kStEScatters] += pk.cnt[4];
+      st.v[kStShellCrossings] += pk.cnt[5];
+      const double e_lab = static_cast<double>(pk.e_lab) * c.e_cmf;
       if (status == 1) {
         int b;
-        if (pk.nu_lab < p.spec_lo) b = p.spec_bins;
+        if (pk.nu_lab < c.spec_lo) b = c.spec_bins;
         else {
-          const double t = (pk.nu_lab - p.spec_lo) / p.spec_dnu;
-          b = (t >= 0.0 && t < static_cast<double>(p.spec_bins)) ? static_cast<int>(floor(t))
-                                                                   : p.spec_bins + 1;
+          const double t = (pk.nu_lab - c.spec_lo) / c.spec_dnu;
+          b = (t >= 0.0 && t < static_cast<double>(c.spec_bins)) ? static_cast<int>(floor(t))
+                                                                   : c.spec_bins + 1;
         }
-        atomicAdd(p.spectrum + b, e_lab);
+        atomicAdd(c.spectrum + b, e_lab);
       }
       if (REC) {
-        p.rec_status[pk.pid - p.first_packet] = status;
-        p.rec_nu[pk.pid - p.first_packet] = pk.nu_lab;
-        p.rec_e[pk.pid - p.first_packet] = e_lab;
+        const uint64_t r = pk.pid - c.first_packet;
+        c.rec_status[r] = status;
+        c.rec_nu[r] = pk.nu_lab;
+        c.rec_e[r] = e_lab;
 #pragma unroll
-        for (int c = 0; c < kNCounters; ++c)
-          p.rec_cnt[static_cast<size_t>(pk.pid - p.first_packet) * kNCounters + c] = pk.cnt[c];
+        for (int k = 0; k < kNCounters; ++k) c.rec_cnt[r * kNCounters + k] = pk.cnt[k];
       }
       alive = false;
     }
   }
-  if (acc_s >= 0) {
-    atomicAdd(p.j_est + acc_s, acc_j * e_cmf0);
-    atomicAdd(p.nu_bar + acc_s, acc_nb * e_cmf0);
-  }
-  unsigned long long st[kNStats] = {n_esc, n_reab, n_cap, n_seg, n_chk, n_res, n_lint, n_esca, n_shell};
-#pragma unroll
-  for (int i = 0; i < kNStats; ++i) {
-    unsigned long long v = st[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0u && v) atomicAdd(p.stats + i, v);
+  if (cur_model >= 0) {
+    if (acc_s >= 0) {
+      atomicAdd(c.j_est + acc_s, acc_j * c.e_cmf);
+      atomicAdd(c.nu_bar + acc_s, acc_nb * c.e_cmf);
+    }
+    flush_stats(st, c.stats);
   }
   if (lane == 0u) atomicMax(p.flags + 2, global_ns());
 }
 
-template <int MODE, bool JB, bool REC>
+template <int MODE, bool JB, bool REC, bool BATCH>
 const void *kptr() {
-  return reinterpret_cast<const void *>(&transport_mixed<MODE, JB, REC>);
+  return reinterpret_cast<const void *>(&transport_mixed<MODE, JB, REC, BATCH>);
+}
+
+template <bool BATCH>
+const void *select_b(int line_mode, bool jb, bool rec) {
+  if (line_mode == 0) {
+    if (jb) return rec ? kptr<0, true, true, BATCH>() : kptr<0, true, false, BATCH>();
+    return rec ? kptr<0, false, true, BATCH>() : kptr<0, false, false, BATCH>();
+  }
+  if (jb) return rec ? kptr<1, true, true, BATCH>() : kptr<1, true, false, BATCH>();
+  return rec ? kptr<1, false, true, BATCH>() : kptr<1, false, false, BATCH>();
 }
 
 }  // namespace
 
-const void *select_mixed_kernel(int line_mode, bool jb, bool rec) {
-  if (line_mode == 0) {
-    if (jb) return rec ? kptr<0, true, true>() : kptr<0, true, false>();
-    return rec ? kptr<0, false, true>() : kptr<0, false, false>();
-  }
-  if (jb) return rec ? kptr<1, true, true>() : kptr<1, true, false>();
-  return rec ? kptr<1, false, true>() : kptr<1, false, false>();
+const void *select_mixed_kernel(int line_mode, bool jb, bool rec) { return select_b<false>(line_mode, jb, rec); }
+
+size_t mixed_smem_bytes(int S) { return 4 * static_cast<size_t>(S) * sizeof(float); }
+
+cudaError_t batch_occupancy(int line_mode, bool j_blue, bool record, int n_models, int *blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      blocks_per_sm, select_b<true>(line_mode, j_blue, record), kBlock,
+      static_cast<size_t>(n_models + 1) * sizeof(unsigned long long));
 }
 
-size_t mixed_smem_bytes(int S) { return static_cast<size_t>(kShellArrays) * S * sizeof(float); }
+cudaError_t launch_transport_batch(const TransportParams &p, int line_mode, bool j_blue, bool record,
+                                   int grid, cudaStream_t st) {
+  void *args[] = {const_cast<TransportParams *>(&p)};
+  return cudaLaunchKernel(select_b<true>(line_mode, j_blue, record), dim3(grid), dim3(kBlock), args,
+                          static_cast<size_t>(p.n_models + 1) * sizeof(unsigned long long), st);
+}
 
 }  // namespace mcgpu

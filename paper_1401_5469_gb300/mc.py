@@ -38,7 +38,9 @@ EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_run_iter
             "mc_update_radiation_field",
             "mc_read_estimators", "mc_read_spectrum", "mc_read_packets", "mc_read_plasma",
             "mc_read_timing", "mc_read_transport_phases", "mc_launch_count", "mc_synchronize", "mc_model_destroy",
-            "mc_status_string", "mc_last_error_message", "mc_transport_noalloc")
+            "mc_status_string", "mc_last_error_message", "mc_transport_noalloc",
+            "mc_batch_create", "mc_batch_run_iteration", "mc_batch_synchronize",
+            "mc_batch_read_timing", "mc_batch_last_error_message", "mc_batch_destroy")
 
 
 class mc_geometry_desc(C.Structure):
@@ -153,6 +155,18 @@ def load(build_if_missing: bool = True):
     L.mc_last_error_message.argtypes = [vp]
     L.mc_transport_noalloc.restype = i32
     L.mc_transport_noalloc.argtypes = [P(mc_noalloc_args), vp]
+    L.mc_batch_create.restype = i32
+    L.mc_batch_create.argtypes = [vp, u32, P(vp)]
+    L.mc_batch_run_iteration.restype = i32
+    L.mc_batch_run_iteration.argtypes = [vp, vp, u32, vp, vp, i32]
+    L.mc_batch_synchronize.restype = i32
+    L.mc_batch_synchronize.argtypes = [vp]
+    L.mc_batch_read_timing.restype = i32
+    L.mc_batch_read_timing.argtypes = [vp, vp]
+    L.mc_batch_last_error_message.restype = C.c_char_p
+    L.mc_batch_last_error_message.argtypes = [vp]
+    L.mc_batch_destroy.restype = None
+    L.mc_batch_destroy.argtypes = [vp]
     _lib = L
     return L
 
@@ -406,3 +420,52 @@ class Model:
 
     def synchronize(self):
         return mc_synchronize(self.h)
+
+
+# ----------------------------------------------------------------- batches
+
+class Batch:
+    """Several mixed-precision Models advanced together (mc_batch_*)."""
+
+    def __init__(self, models):
+        self.models = list(models)
+        L = load()
+        arr = (C.c_void_p * len(self.models))(*[m.h.value for m in self.models])
+        self._arr = arr
+        h = C.c_void_p()
+        rc = L.mc_batch_create(C.cast(arr, C.c_void_p), len(self.models), C.byref(h))
+        _check(rc, None)
+        self.h = h
+
+    def _bcheck(self, rc):
+        if rc == MC_OK or rc > 0:
+            return rc
+        msg = load().mc_batch_last_error_message(self.h).decode() or load().mc_status_string(rc).decode()
+        raise MCError(rc, msg)
+
+    def run_iteration(self, seeds, iteration, n_packets, t_inner, update=True):
+        n = len(self.models)
+        s = np.ascontiguousarray(np.broadcast_to(np.asarray(seeds, dtype=np.uint64), (n,)))
+        npk = np.ascontiguousarray(np.broadcast_to(np.asarray(n_packets, dtype=np.uint64), (n,)))
+        t = np.ascontiguousarray(np.broadcast_to(np.asarray(t_inner, dtype=np.float64), (n,)))
+        return self._bcheck(load().mc_batch_run_iteration(self.h, _p(s), int(iteration), _p(npk), _p(t),
+                                                          int(bool(update))))
+
+    def synchronize(self):
+        return self._bcheck(load().mc_batch_synchronize(self.h))
+
+    def transport_ms(self):
+        ms = np.zeros(1, dtype=np.float32)
+        self._bcheck(load().mc_batch_read_timing(self.h, _p(ms)))
+        return float(ms[0])
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().mc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
