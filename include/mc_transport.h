@@ -254,14 +254,15 @@ void mc_model_destroy(mc_model *m);
  * per model with mc_read_estimators / mc_read_spectrum / mc_read_plasma /
  * mc_read_packets (ordered after the batch on the models' stream).  A model in
  * a batch cannot be run alone until the batch is destroyed.
- *  seeds, n_packets, t_inner: [n_models] in the order passed to
- *  mc_batch_create.  Errors: MC_ERR_INVALID_ARG, MC_ERR_UNSUPPORTED (a model
+ *  seeds, iterations, n_packets, t_inner: [n_models] in the order passed to
+ *  mc_batch_create; model i runs its iteration iterations[i] with seeds[i]
+ *  (the same draws as mc_run_iteration(m, seeds[i], iterations[i], ...)).  Errors: MC_ERR_INVALID_ARG, MC_ERR_UNSUPPORTED (a model
  *  not in mixed precision), MC_ERR_NOT_READY (no plasma state), MC_ERR_CUDA;
  *  messages via mc_batch_last_error_message. */
 typedef struct mc_batch mc_batch;
 
 mc_status mc_batch_create(mc_model *const *models, uint32_t n_models, mc_batch **out);
-mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, uint32_t iteration,
+mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, const uint32_t *iterations,
                                  const uint64_t *n_packets, const double *t_inner, int32_t update);
 mc_status mc_batch_synchronize(mc_batch *b);
 /* Device time of the last batched transport launch, ms[0] (synchronises). */

@@ -37,6 +37,8 @@ struct mc_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<int> graph_shape;    // per model: 1 if its Sobolev depths were recomputed
   std::vector<uint32_t> graph_order;  // launch order captured in the graph
+  std::vector<uint64_t> graph_np;     // per-model packets (packet energy is baked into the graph)
+  std::vector<double> graph_tin;      // per-model T_inner
   bool graph_update = false;
   uint64_t graph_total = 0;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
@@ -79,6 +81,10 @@ mc_status enqueue_iteration(mc_batch *b, int update) {
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->t1, b->stream, cudaEventRecordExternal);
   if (e != cudaSuccess) return bcuda(b, e, "batched transport");
   b->launches += 1;
+  for (size_t k = 0; k < b->models.size(); ++k) {
+    const mc_status rc = model_finish_transport(b->models[k], b->h_params[k], b->stream);
+    if (rc != MC_OK) return bfail(b, rc, b->models[k]->err);
+  }
   if (update) {
     for (mc_model *m : b->models) {
       const mc_status rc = model_update(m, b->stream, false);
@@ -144,9 +150,9 @@ mc_status mc_batch_create(mc_model *const *models, uint32_t n_models, mc_batch *
   return MC_OK;
 }
 
-mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, uint32_t iteration,
+mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, const uint32_t *iterations,
                                  const uint64_t *n_packets, const double *t_inner, int32_t update) {
-  if (!b || !seeds || !n_packets || !t_inner) return MC_ERR_INVALID_ARG;
+  if (!b || !seeds || !iterations || !n_packets || !t_inner) return MC_ERR_INVALID_ARG;
   const size_t n = b->models.size();
   // the previous iteration's graph reads the pinned parameter table when it
   // starts; wait until it has been copied before overwriting it
@@ -178,7 +184,7 @@ mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, uint32_t it
   for (size_t k = 0; k < n; ++k) {
     const uint32_t i = order[k];
     mc_model *m = b->models[k];
-    model_fill_transport(m, b->h_params[k], seeds[i], iteration, 0, n_packets[i], n_packets[i], t_inner[i]);
+    model_fill_transport(m, b->h_params[k], seeds[i], iterations[i], 0, n_packets[i], n_packets[i], t_inner[i]);
     b->h_prefix[k + 1] = b->h_prefix[k] + n_packets[i];
     shape[k] = (!m->tau_given && m->tau_dirty) ? 1 : 0;
   }
@@ -193,7 +199,10 @@ mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, uint32_t it
   }
   if (e != cudaSuccess) return bcuda(b, e, "stream order");
 
+  const std::vector<uint64_t> np(n_packets, n_packets + n);
+  const std::vector<double> tin(t_inner, t_inner + n);
   const bool reuse = b->exec && b->graph_shape == shape && b->graph_order == order &&
+                     b->graph_np == np && b->graph_tin == tin &&
                      b->graph_update == (update != 0) &&
                      b->graph_total == b->h_prefix[n];
   if (!reuse) {
@@ -211,6 +220,8 @@ mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, uint32_t it
     if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
     b->graph_shape = shape;
     b->graph_order = order;
+    b->graph_np = np;
+    b->graph_tin = tin;
     b->graph_update = update != 0;
     b->graph_total = b->h_prefix[n];
   } else {

@@ -268,7 +268,8 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
             alloc_n(m, &m->counters, static_cast<size_t>(kNCounterSlots)) &&
             alloc_n(m, &m->planck_cdf, static_cast<size_t>(kPlanckLmax) + 1);
   if (ok && run->j_blue) ok = alloc_n(m, &m->j_blue, SL);
-  if (ok && run->precision == MC_PRECISION_MIXED) ok = alloc_n(m, &m->shell32, 4 * static_cast<size_t>(S));
+  if (ok && run->precision == MC_PRECISION_MIXED)
+    ok = alloc_n(m, &m->shell32, 4 * static_cast<size_t>(S)) && alloc_n(m, &m->est_fix, 2 * static_cast<size_t>(S));
   if (ok && meta) ok = alloc_n(m, &m->line_row, L) && alloc_n(m, &m->lev_l, L) && alloc_n(m, &m->lev_u, L);
   if (ok && atomic) {
     const size_t IK = static_cast<size_t>(I) * K;
@@ -472,6 +473,8 @@ mc_status mc_run_iteration_range(mc_model *m, uint64_t seed, uint32_t iteration,
   if (e != cudaSuccess) return cuda_fail(m, e, "transport kernel");
   cudaEventRecord(m->ev[kEvTransport1], m->stream);
   m->launches += 1;
+  st = model_finish_transport(m, p, m->stream);
+  if (st != MC_OK) return st;
   m->have_run = true;
   m->ran_update = false;
   m->last_n = n_packets;
@@ -505,6 +508,19 @@ mc_status model_prepare(mc_model *m, cudaStream_t st, bool events) {
     if (e != cudaSuccess) return cuda_fail(m, e, "zero j_blue");
     m->launches += 1;
   }
+  if (m->est_fix) {
+    e = cudaMemsetAsync(m->est_fix, 0, 2 * static_cast<size_t>(m->S) * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(m, e, "zero fixed-point estimators");
+  }
+  return MC_OK;
+}
+
+mc_status model_finish_transport(mc_model *m, const TransportParams &p, cudaStream_t st) {
+  if (!m->est_fix) return MC_OK;
+  const cudaError_t e = launch_est_from_fix(m->est_fix, static_cast<int>(m->S), p.e_cmf, p.nu_scale,
+                                            m->j_est, m->nu_bar, st);
+  if (e != cudaSuccess) return cuda_fail(m, e, "estimator conversion");
+  m->launches += 1;
   return MC_OK;
 }
 
@@ -542,6 +558,8 @@ void model_fill_transport(const mc_model *m, TransportParams &p, uint64_t seed, 
   p.rec_status = m->rec_status; p.rec_nu = m->rec_nu; p.rec_e = m->rec_e; p.rec_cnt = m->rec_cnt;
   p.timeout_ns = m->run.timeout_ns;
   p.shell32 = m->shell32;
+  p.est_fix = m->est_fix;
+  p.inv_nu_ref = 1.0 / p.nu_scale;
 }
 
 mc_status model_update(mc_model *m, cudaStream_t st, bool events) {

@@ -78,6 +78,8 @@ struct TransportParams {
   double *rec_nu, *rec_e;
   unsigned long long *rec_cnt;       // [n * kNCounters]
   const float *shell32;              // [4 S] binary32 shell table (mixed; batched launch)
+  unsigned long long *est_fix;       // [2 S] mixed: J, nu_bar sums in fixed point (see below)
+  double inv_nu_ref;                 // mixed: 1 / (k T_inner / h), scale of nu in nu_bar
   const TransportParams *batch;      // batched launch: per-model parameters, or nullptr
   const unsigned long long *batch_prefix;  // [n_models + 1] packet offsets of the models
   int32_t n_models;
@@ -87,6 +89,15 @@ struct TransportParams {
 };
 
 constexpr int kNCounterSlots = kNStats + 5;  // stats, work counter, flags[4]
+
+// Mixed precision accumulates the J and nu_bar estimators as unsigned 64-bit
+// fixed point: each segment's contribution (in units of the packet energy E,
+// and nu_cmf in units of k T_inner / h) is rounded to a multiple of 2^-32 and
+// added with integer atomics, so the sums do not depend on the order in which
+// packets finish (the radiation-field update, and every later iteration, are
+// then the same whatever the launch mixes).  Headroom: 2^64 / 2^32 = 4.3e9
+// units per shell.
+constexpr double kEstFixScale = 0x1.0p32;
 
 struct PlasmaParams {
   int32_t S, I, K, L;
@@ -123,6 +134,9 @@ cudaError_t launch_transport_batch(const TransportParams &p, int line_mode, bool
                                    int grid, cudaStream_t st);
 size_t mixed_smem_bytes(int S);
 cudaError_t launch_to_f32(const double *in, float *out, size_t n, cudaStream_t st);
+// j_est = fix[s] 2^-32 E, nu_bar = fix[S + s] 2^-32 E nu_ref (mixed precision).
+cudaError_t launch_est_from_fix(const unsigned long long *fix, int S, double e_cmf, double nu_ref,
+                                double *j_est, double *nu_bar, cudaStream_t st);
 cudaError_t launch_populations(const PlasmaParams &p, cudaStream_t st);
 cudaError_t launch_sobolev_tau(const PlasmaParams &p, cudaStream_t st);
 cudaError_t launch_update(const UpdateParams &p, cudaStream_t st);

@@ -34,6 +34,7 @@ struct mc_model {
   double *x_in = nullptr, *x_out = nullptr, *inv_x_in = nullptr, *inv_x_out = nullptr;
   double *kappa = nullptr, *inv_kappa = nullptr;
   float *shell32 = nullptr;  // [4 S] binary32 x_in^2, x_out^2, kappa', 1/kappa' (mixed precision)
+  unsigned long long *est_fix = nullptr;  // [2 S] fixed-point J, nu_bar sums (mixed precision)
   mcgpu::DbrRec *dbr_rec = nullptr, *dbr_bucket = nullptr;
   unsigned long long *row_info = nullptr;
   float *kappa32 = nullptr, *x_in32 = nullptr, *x_out32 = nullptr;
@@ -77,6 +78,10 @@ mc_status model_prepare(mc_model *m, cudaStream_t st, bool events);
 // Transport parameters of packets [first, first+n) of an n_total iteration.
 void model_fill_transport(const mc_model *m, TransportParams &p, uint64_t seed, uint32_t iteration,
                           uint64_t first, uint64_t n, uint64_t n_total, double t_inner);
+
+// After the transport launch: turn the fixed-point J, nu_bar sums of a
+// mixed-precision model into the binary64 estimators (no-op otherwise).
+mc_status model_finish_transport(mc_model *m, const TransportParams &p, cudaStream_t st);
 
 // Eqs. 15-16 for this model on `st`; marks the Sobolev depths stale.
 mc_status model_update(mc_model *m, cudaStream_t st, bool events);

@@ -164,6 +164,14 @@ __global__ void row_info_kernel(uint32_t L, const int32_t *line_row, const uint3
   row_info[j] = b | (n << 32);
 }
 
+__global__ void est_from_fix_kernel(const unsigned long long *fix, int S, double e_cmf, double nu_ref,
+                                    double *j_est, double *nu_bar) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  j_est[s] = (static_cast<double>(fix[s]) * (1.0 / kEstFixScale)) * e_cmf;
+  nu_bar[s] = ((static_cast<double>(fix[S + s]) * (1.0 / kEstFixScale)) * e_cmf) * nu_ref;
+}
+
 __global__ void to_f32_kernel(const double *in, float *out, size_t n) {
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n; i += stride)
@@ -233,6 +241,12 @@ cudaError_t launch_dbr_setup(uint32_t nnz, uint32_t n_rows, uint32_t L, int K,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   row_info_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, line_row, dbr_offset, row_info);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_est_from_fix(const unsigned long long *fix, int S, double e_cmf, double nu_ref,
+                                double *j_est, double *nu_bar, cudaStream_t st) {
+  est_from_fix_kernel<<<(S + 63) / 64, 64, 0, st>>>(fix, S, e_cmf, nu_ref, j_est, nu_bar);
   return cudaGetLastError();
 }
 

@@ -32,7 +32,7 @@ constexpr int kLineEvent = 1, kElectronEvent = 2, kShellEvent = 3;
 
 struct PacketM {
   double nu_lab;               // binary64
-  float p, q, r2;              // x mu, x^2 - p^2, x^2
+  float p, q;                  // x mu, x^2 - p^2
   float e_lab, inv_nu, inv_D;  // e_lab relative to the injection energy
   int32_t shell, next_line;
   uint32_t pid;
@@ -49,6 +49,8 @@ struct MCtx {
   const DbrRec *bucket, *rec;
   double *j_blue, *j_est, *nu_bar, *spectrum;
   unsigned long long *stats;
+  unsigned long long *est_fix;  // [2 S] J, nu_bar in fixed point
+  double inv_nu_ref;
   const double *planck;
   int32_t S, L, spec_bins;
   uint32_t key0, key1, iteration;
@@ -77,6 +79,8 @@ __device__ __forceinline__ void load_ctx(MCtx &c, const TransportParams &q, cons
   c.nu_bar = q.nu_bar;
   c.spectrum = q.spectrum;
   c.stats = q.stats;
+  c.est_fix = q.est_fix;
+  c.inv_nu_ref = q.inv_nu_ref;
   c.planck = q.planck_cdf;
   c.spec_bins = q.spec_bins;
   c.key0 = q.key0;
@@ -148,7 +152,10 @@ __device__ __forceinline__ void flush_stats(Stats &st, unsigned long long *dst) 
   }
 }
 
-template <int MODE, bool JB, bool REC, bool BATCH>
+// One kernel serves a single model (p.n_models == 0) and a batch: the two
+// launches run the same machine code, so a model's results do not depend on
+// the company it is launched in.
+template <int MODE, bool JB, bool REC>
 __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams p) {
   extern __shared__ unsigned long long smem_u64[];
   const unsigned lane = threadIdx.x & 31u;
@@ -156,7 +163,8 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
   MCtx c;
   int32_t cur_model = -1;
   unsigned long long *prefix = smem_u64;
-  if (BATCH) {
+  const bool batch = p.n_models > 0;
+  if (batch) {
     for (int i = threadIdx.x; i <= p.n_models; i += blockDim.x) prefix[i] = p.batch_prefix[i];
     __syncthreads();
   } else {
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
 #pragma unroll
   for (int i = 0; i < kNStats; ++i) st.v[i] = 0ull;
   int32_t acc_s = -1;
-  double acc_j = 0.0, acc_nb = 0.0;
+  unsigned long long acc_j = 0ull, acc_nb = 0ull;  // fixed point, see kEstFixScale
 
   for (;;) {
     const bool need = !alive && !finished;
@@ -190,7 +198,7 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
       if (need) {
         unsigned long long id = base + __popc(needmask & lanemask_lt);
         if (id < p.n_packets) {
-          if (BATCH) {
+          if (batch) {
             int lo = 0, hi = p.n_models;  // model m with prefix[m] <= id < prefix[m+1]
             while (hi - lo > 1) {
               const int mid = (lo + hi) >> 1;
@@ -199,12 +207,12 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
             if (lo != cur_model) {
               if (cur_model >= 0) {
                 if (acc_s >= 0) {
-                  atomicAdd(c.j_est + acc_s, acc_j * c.e_cmf);
-                  atomicAdd(c.nu_bar + acc_s, acc_nb * c.e_cmf);
+                  atomicAdd(c.est_fix + acc_s, acc_j);
+                  atomicAdd(c.est_fix + c.S + acc_s, acc_nb);
                 }
                 flush_stats(st, c.stats);
               }
-              acc_s = -1; acc_j = 0.0; acc_nb = 0.0;
+              acc_s = -1; acc_j = 0ull; acc_nb = 0ull;
               load_ctx(c, p.batch[lo], p.batch[lo].shell32);
               cur_model = lo;
             }
@@ -225,7 +233,6 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
           const float D = 1.0f - pp;
           const float iD = 1.0f / D;
           pk.p = pp;
-          pk.r2 = c.x0sq;
           pk.q = max0f(fmaf(-pp, pp, c.x0sq));
           pk.nu_lab = nu_cmf * static_cast<double>(iD);
           pk.e_lab = iD;  // E_lab / E_cmf(injection)
@@ -262,7 +269,7 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
       pk.cnt[0] += 1u;
       const int32_t s = pk.shell;
       const int32_t L = c.L;
-      const float pp = pk.p, q = pk.q, r2 = pk.r2, inv_nu = pk.inv_nu;
+      const float pp = pk.p, q = pk.q, inv_nu = pk.inv_nu;
       const double nu_lab = pk.nu_lab;
       const float Df = 1.0f - pp;
       const float inv_D = pk.have_inv_D ? pk.inv_D : 1.0f / Df;
@@ -349,23 +356,22 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         if (key_e > key_shell) { kind = kElectronEvent; l = max0f(static_cast<float>(nu_cmf - thr_e) * inv_nu); }
         else { kind = kShellEvent; l = max0f(p_exit - pp); }
       }
-      // estimators (binary32 contribution, binary64 sums in units of E)
+      // estimators: binary32 contribution (units of E), summed in fixed point
       const double wgt = static_cast<double>(eD2 * l);
       if (s != acc_s) {
         if (acc_s >= 0) {
-          atomicAdd(c.j_est + acc_s, acc_j * c.e_cmf);
-          atomicAdd(c.nu_bar + acc_s, acc_nb * c.e_cmf);
+          atomicAdd(c.est_fix + acc_s, acc_j);
+          atomicAdd(c.est_fix + c.S + acc_s, acc_nb);
         }
-        acc_s = s; acc_j = 0.0; acc_nb = 0.0;
+        acc_s = s; acc_j = 0ull; acc_nb = 0ull;
       }
-      acc_j += wgt;
-      acc_nb = fma(wgt, nu_cmf, acc_nb);
+      acc_j += __double2ull_rn(wgt * kEstFixScale);
+      acc_nb += __double2ull_rn((wgt * (nu_cmf * c.inv_nu_ref)) * kEstFixScale);
       pk.next_line = j;
       if (kind == kShellEvent) {
         pk.cnt[5] += 1u;
         const int32_t ns = inner ? s - 1 : s + 1;
         pk.p = p_exit;
-        pk.r2 = inner ? xi2 : xo2;
         pk.shell = ns;
         pk.have_inv_D = false;
         if (ns >= c.S) status = 1;
@@ -404,7 +410,6 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         const double r1 = fma(r0, fma(-D2d, r0, 1.0), r0);
         pk.p = pn;
         pk.q = max0f(fmaf(-pn, pn, r2n));
-        pk.r2 = r2n;
         pk.nu_lab = nu_c * r1;
         pk.e_lab = e_c * iD2;
         pk.inv_nu = inv_nu_c * D2;
@@ -446,45 +451,44 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
   }
   if (cur_model >= 0) {
     if (acc_s >= 0) {
-      atomicAdd(c.j_est + acc_s, acc_j * c.e_cmf);
-      atomicAdd(c.nu_bar + acc_s, acc_nb * c.e_cmf);
+      atomicAdd(c.est_fix + acc_s, acc_j);
+      atomicAdd(c.est_fix + c.S + acc_s, acc_nb);
     }
     flush_stats(st, c.stats);
   }
   if (lane == 0u) atomicMax(p.flags + 2, global_ns());
 }
 
-template <int MODE, bool JB, bool REC, bool BATCH>
+template <int MODE, bool JB, bool REC>
 const void *kptr() {
-  return reinterpret_cast<const void *>(&transport_mixed<MODE, JB, REC, BATCH>);
+  return reinterpret_cast<const void *>(&transport_mixed<MODE, JB, REC>);
 }
 
-template <bool BATCH>
 const void *select_b(int line_mode, bool jb, bool rec) {
   if (line_mode == 0) {
-    if (jb) return rec ? kptr<0, true, true, BATCH>() : kptr<0, true, false, BATCH>();
-    return rec ? kptr<0, false, true, BATCH>() : kptr<0, false, false, BATCH>();
+    if (jb) return rec ? kptr<0, true, true>() : kptr<0, true, false>();
+    return rec ? kptr<0, false, true>() : kptr<0, false, false>();
   }
-  if (jb) return rec ? kptr<1, true, true, BATCH>() : kptr<1, true, false, BATCH>();
-  return rec ? kptr<1, false, true, BATCH>() : kptr<1, false, false, BATCH>();
+  if (jb) return rec ? kptr<1, true, true>() : kptr<1, true, false>();
+  return rec ? kptr<1, false, true>() : kptr<1, false, false>();
 }
 
 }  // namespace
 
-const void *select_mixed_kernel(int line_mode, bool jb, bool rec) { return select_b<false>(line_mode, jb, rec); }
+const void *select_mixed_kernel(int line_mode, bool jb, bool rec) { return select_b(line_mode, jb, rec); }
 
 size_t mixed_smem_bytes(int S) { return 4 * static_cast<size_t>(S) * sizeof(float); }
 
 cudaError_t batch_occupancy(int line_mode, bool j_blue, bool record, int n_models, int *blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, select_b<true>(line_mode, j_blue, record), kBlock,
+      blocks_per_sm, select_b(line_mode, j_blue, record), kBlock,
       static_cast<size_t>(n_models + 1) * sizeof(unsigned long long));
 }
 
 cudaError_t launch_transport_batch(const TransportParams &p, int line_mode, bool j_blue, bool record,
                                    int grid, cudaStream_t st) {
   void *args[] = {const_cast<TransportParams *>(&p)};
-  return cudaLaunchKernel(select_b<true>(line_mode, j_blue, record), dim3(grid), dim3(kBlock), args,
+  return cudaLaunchKernel(select_b(line_mode, j_blue, record), dim3(grid), dim3(kBlock), args,
                           static_cast<size_t>(p.n_models + 1) * sizeof(unsigned long long), st);
 }
 

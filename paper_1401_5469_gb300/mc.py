@@ -158,7 +158,7 @@ def load(build_if_missing: bool = True):
     L.mc_batch_create.restype = i32
     L.mc_batch_create.argtypes = [vp, u32, P(vp)]
     L.mc_batch_run_iteration.restype = i32
-    L.mc_batch_run_iteration.argtypes = [vp, vp, u32, vp, vp, i32]
+    L.mc_batch_run_iteration.argtypes = [vp, vp, vp, vp, vp, i32]
     L.mc_batch_synchronize.restype = i32
     L.mc_batch_synchronize.argtypes = [vp]
     L.mc_batch_read_timing.restype = i32
@@ -443,12 +443,14 @@ class Batch:
         msg = load().mc_batch_last_error_message(self.h).decode() or load().mc_status_string(rc).decode()
         raise MCError(rc, msg)
 
-    def run_iteration(self, seeds, iteration, n_packets, t_inner, update=True):
+    def run_iteration(self, seeds, iterations, n_packets, t_inner, update=True):
+        """Model i runs its iteration iterations[i] with seeds[i] (scalars broadcast)."""
         n = len(self.models)
         s = np.ascontiguousarray(np.broadcast_to(np.asarray(seeds, dtype=np.uint64), (n,)))
+        its = np.ascontiguousarray(np.broadcast_to(np.asarray(iterations, dtype=np.uint32), (n,)))
         npk = np.ascontiguousarray(np.broadcast_to(np.asarray(n_packets, dtype=np.uint64), (n,)))
         t = np.ascontiguousarray(np.broadcast_to(np.asarray(t_inner, dtype=np.float64), (n,)))
-        return self._bcheck(load().mc_batch_run_iteration(self.h, _p(s), int(iteration), _p(npk), _p(t),
+        return self._bcheck(load().mc_batch_run_iteration(self.h, _p(s), _p(its), _p(npk), _p(t),
                                                           int(bool(update))))
 
     def synchronize(self):

@@ -1,0 +1,174 @@
+"""Continuous-batching service for spectral-fit model evaluations.
+
+Each request is one ejecta model to be iterated K times (Sect. 2.8: Sobolev
+depths from T_R and W, Monte Carlo transport, T_R/W update) in mixed
+precision.  The service keeps every admitted model resident on the GPU
+(plasma state, line data and estimators stay in device memory across its
+iterations) and advances all resident models together, one batched transport
+launch (a captured CUDA graph) per tick.  Requests that arrive while others
+are on the GPU are admitted at the next tick if the HBM budget allows, so
+their iterations overlap on the device with the models already running; a
+model leaves as soon as its last iteration is done.
+
+A request's results depend only on its own model, seed and iteration count:
+packet draws are keyed by (seed, iteration, packet), single and batched
+launches run the same kernel, and J, nu_bar are summed in fixed point, so the
+same request gives bit-identical J, nu_bar, T_R and W alone and in any mix
+(only the binary64 J_blue and spectrum sums depend on summation order).
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from collections import deque
+from typing import Deque, Dict, List, Optional
+
+import numpy as np
+
+from . import mc
+
+
+def model_footprint_bytes(spec, j_blue: Optional[bool] = None) -> int:
+    """Device bytes a mixed-precision model holds (Sobolev depths, J_blue,
+    line list, branching tables, level data, spectrum)."""
+    S, L = spec.n_shells, spec.n_lines
+    jb = spec.j_blue if j_blue is None else j_blue
+    nnz = L if spec.dbr_line is None else int(spec.dbr_line.shape[0])
+    b = 4 * S * L                      # binary32 Sobolev depths
+    b += 8 * S * L if jb else 0        # J_blue sums
+    b += L * (8 + 8 + 4 * 3 + 8 + 8)   # nu, f, ion/lower/upper, per-line constants, row info
+    b += L * (4 * 3 + 8)               # staged line arrays used at set-up
+    b += nnz * (4 + 4 + 8 + 32 + 32)   # branching table + guide records
+    if spec.n_ions:
+        b += spec.n_ions * spec.n_levels * (8 + 8 + 1) + S * spec.n_ions * (8 + 8 * spec.n_levels)
+    b += 8 * (spec.spec_bins + 2) + 64 * S + 16 * 1024
+    return int(b)
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    spec: object
+    n_iterations: int
+    seed: int
+    arrival: float = 0.0            # seconds on the service clock
+    admitted: Optional[float] = None
+    finished: Optional[float] = None
+    done_iterations: int = 0
+    t_rad: Optional[np.ndarray] = None
+    w: Optional[np.ndarray] = None
+    j_est: Optional[np.ndarray] = None
+    nu_bar: Optional[np.ndarray] = None
+    spectrum: Optional[np.ndarray] = None
+    keep_history: bool = False
+    history: List = dataclasses.field(default_factory=list)
+
+    @property
+    def latency(self) -> Optional[float]:
+        return None if self.finished is None else self.finished - self.arrival
+
+
+class Server:
+    """Admits requests under an HBM budget and advances all resident models
+    with one batched launch per tick."""
+
+    def __init__(self, hbm_budget_bytes: float = 150e9, j_blue: bool = True, stream=None):
+        self.budget = float(hbm_budget_bytes)
+        self.j_blue = j_blue
+        self.stream = stream
+        self.queue: Deque[Request] = deque()
+        self.active: Dict[int, tuple] = {}   # rid -> (request, model, bytes)
+        self.used = 0
+        self.batch: Optional[mc.Batch] = None
+        self.batch_ids: List[int] = []
+        self.done: List[Request] = []
+        self.ticks = 0
+        self.tick_ms: List[float] = []
+        self.transport_ms: List[float] = []
+
+    # -- admission
+    def submit(self, req: Request):
+        self.queue.append(req)
+
+    def _admit(self, now: float):
+        while self.queue:
+            req = self.queue[0]
+            need = model_footprint_bytes(req.spec, self.j_blue)
+            if self.active and self.used + need > self.budget:
+                break
+            self.queue.popleft()
+            m = mc.Model(req.spec, precision=mc.MC_PRECISION_MIXED, j_blue=self.j_blue,
+                         stream=self.stream)
+            m.set_plasma()
+            req.admitted = now
+            self.active[req.rid] = (req, m, need)
+            self.used += need
+
+    def _retire(self, rid: int, now: float):
+        req, m, need = self.active.pop(rid)
+        req.finished = now
+        m.close()
+        self.used -= need
+        self.done.append(req)
+
+    # -- one tick: every resident model advances by one iteration
+    def step(self, now: float) -> int:
+        self._admit(now)
+        if not self.active:
+            return 0
+        ids = sorted(self.active)
+        if ids != self.batch_ids:
+            if self.batch is not None:
+                self.batch.close()
+            self.batch = mc.Batch([self.active[r][1] for r in ids])
+            self.batch_ids = ids
+        reqs = [self.active[r][0] for r in ids]
+        t0 = time.perf_counter()
+        # each model runs its own next iteration (draws keyed by its seed and index)
+        self.batch.run_iteration([r.seed for r in reqs], [r.done_iterations for r in reqs],
+                                 [r.spec.n_packets for r in reqs], [r.spec.t_inner for r in reqs],
+                                 update=True)
+        self.batch.synchronize()
+        self.tick_ms.append(1e3 * (time.perf_counter() - t0))
+        self.transport_ms.append(self.batch.transport_ms())
+        self.ticks += 1
+        finished = []
+        for r in reqs:
+            m = self.active[r.rid][1]
+            r.done_iterations += 1
+            if r.keep_history:
+                j, nb, _, _ = m.estimators()
+                r.history.append((j, nb) + _radiation_field(m))
+            if r.done_iterations >= r.n_iterations:
+                r.j_est, r.nu_bar, _, _ = m.estimators()
+                r.spectrum = m.spectrum()[0]
+                r.t_rad, r.w = _radiation_field(m)
+                finished.append(r.rid)
+        end = now + (time.perf_counter() - t0)
+        if finished and self.batch is not None:
+            self.batch.close()  # the batch goes before its models
+            self.batch = None
+            self.batch_ids = []
+        for rid in finished:
+            self._retire(rid, end)
+        return len(reqs)
+
+    def close(self):
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
+        for rid in list(self.active):
+            self._retire(rid, time.perf_counter())
+
+
+def _radiation_field(m):
+    t, w = np.zeros(m.S), np.zeros(m.S)
+    mc.mc_read_plasma(m.h, t, w, None)
+    return t, w
+
+
+def percentiles(values, qs=(50, 95, 99)):
+    v = np.asarray([x for x in values if x is not None], dtype=float)
+    if v.size == 0:
+        return {f"p{q}": None for q in qs}
+    return {f"p{q}": float(np.percentile(v, q)) for q in qs}
