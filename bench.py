@@ -8,10 +8,28 @@ iteration of Sect. 2.8: Sobolev depths recomputed from the current T_R, W
 updated from the estimators.  The iteration index advances every step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --workload batched [--models M]
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle (the plain
 FP64 C implementation used by the tests) on a bounded packet sample of the
 same workload.
+
+``--workload batched``: 256 ejecta models of uneven size (shells U{10..40},
+lines U{5e4..5e5}, packets log-uniform in [1e4, 1e6], velocities, epoch and
+T_inner drawn per model), 10 iterations each with the T_R/W update.  The
+batched mixed-precision path (one persistent launch per iteration for all
+models, a captured CUDA graph, autotuned launch shape) is timed against the
+plain per-model binary64 path on the same models, seeds and packet counts;
+the metric is models/s (models completed with all 10 iterations per second).
+
+``--workload serve [--precision mixed|fp64] [--rate R]``: continuous-batching
+service.  Requests arrive as a Poisson process (R = 50 models/s by default)
+for 70 s; each is one model of the batched workload's distribution with
+U{5..20} iterations.  Resident models are admitted first come, first served
+under a 150 GB HBM budget and a per-tick packet budget.  The first 10 s are
+warm-up; models/s and the p50/p95/p99 latency (arrival to last iteration) are
+taken over the requests that arrive in the remaining 60 s and finish by its
+end, with the backlog left at the end reported beside them.
 """
 from __future__ import annotations
 
@@ -317,15 +335,220 @@ def measure_mixed(spec, seed, args):
             "transport_tail_ms": tail / args.steps, "dtype": "f32/f64"}
 
 
+def _log(msg):
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
+def run_batched(args):
+    """256 uneven models x 10 iterations: batched mixed vs per-model binary64."""
+    import torch
+    from paper_1401_5469_gb300 import mc, synth
+    torch.cuda.set_device(0)
+    n_models, n_it = args.models, 10
+    t0 = time.perf_counter()
+    specs = synth.batched_models(n_models=n_models, seed=1401, iterations=n_it)
+    _log(f"generated {n_models} models in {time.perf_counter() - t0:.1f} s")
+    seeds = [5469 + k for k in range(n_models)]
+    n = [s.n_packets for s in specs]
+    t_in = [s.t_inner for s in specs]
+    total_packets = int(sum(n))
+    stream = torch.cuda.current_stream()
+
+    # ---- batched, mixed precision
+    t0 = time.perf_counter()
+    models = [mc.Model(s, precision=mc.MC_PRECISION_MIXED) for s in specs]
+    for m in models:
+        m.set_plasma()
+    b = mc.Batch(models)
+    torch.cuda.synchronize()
+    _log(f"created mixed models in {time.perf_counter() - t0:.1f} s")
+    t0 = time.perf_counter()
+    tuned, tuned_ms, trials = b.autotune(seeds, 0, n, t_in)
+    tune_s = time.perf_counter() - t0
+    _log(f"autotune {tuned} {tuned_ms:.1f} ms after {trials} trials ({tune_s:.1f} s)")
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    transport_ms = []
+    w0 = time.perf_counter()
+    ev0.record(stream)
+    for it in range(n_it):
+        b.run_iteration(seeds, it, n, t_in, update=True)
+        transport_ms.append(b.transport_ms())
+    b.synchronize()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall_b = time.perf_counter() - w0
+    batched_s = ev0.elapsed_time(ev1) / 1e3
+    clk = clocks.stop()
+    t_mixed = []
+    for m in models:
+        t, w, _ = m.plasma()
+        t_mixed.append(t)
+    b.close()
+    for m in models:
+        m.close()
+    _log(f"batched: {batched_s:.2f} s for {n_it} iterations")
+
+    # ---- per-model binary64, the same models, seeds and packets
+    limit = int(os.environ.get("BENCH_FP64_MODELS", str(n_models)))
+    fp64_s = 0.0
+    t_fp64 = []
+
+    def fp64_loop(spec, seed):
+        m = mc.Model(spec)
+        m.set_plasma()
+        for it in range(n_it):
+            m.run_iteration(seed, it, spec.n_packets, spec.t_inner)
+            mc.mc_update_radiation_field(m.h, None, None)
+        m.synchronize()
+        t, _, _ = m.plasma()
+        m.close()
+        return t
+
+    for k, spec in enumerate(specs[:limit]):
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        t_fp64.append(fp64_loop(spec, seeds[k]))
+        fp64_s += time.perf_counter() - w0
+    fp64_models_s = limit / fp64_s if limit else None
+    _log(f"per-model fp64: {fp64_s:.2f} s for {limit} models")
+    # Monte Carlo noise of the same statistic: binary64 with another seed
+    rms = lambda a, b_: float(np.sqrt(np.mean(((a - b_) / b_) ** 2)))
+    n_noise = min(16, limit)
+    d_mix = [rms(t_mixed[k], t_fp64[k]) for k in range(limit)]
+    d_seed = [rms(fp64_loop(specs[k], seeds[k] + 1_000_000), t_fp64[k]) for k in range(n_noise)]
+    med = lambda v: float(np.median(v)) if v else None
+    value = n_models / batched_s
+    line = {
+        "metric": "models/s", "value": value, "unit": "models/s", "n_gpus": 1, "steps": n_it,
+        "warmup": trials, "ms_per_step": 1e3 * batched_s / n_it, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": f"batched-{n_models}-uneven-models-10-iterations",
+                   "models": n_models, "iterations": n_it, "packets_per_iteration": total_packets,
+                   "shells": [min(s.n_shells for s in specs), max(s.n_shells for s in specs)],
+                   "lines": [min(s.n_lines for s in specs), max(s.n_lines for s in specs)],
+                   "j_blue": bool(specs[0].j_blue), "line_mode": "downbranch",
+                   "l2": "inputs larger than L2 (Sobolev depths and J_blue of all models)"},
+        "packets_per_s": total_packets * n_it / batched_s,
+        "wall_s": wall_b,
+        "transport_ms_per_iteration": transport_ms,
+        "autotune": {"launch": tuned, "transport_ms": tuned_ms, "trials": trials, "seconds": tune_s},
+        "fp64_per_model": {"models_per_s": fp64_models_s, "seconds": fp64_s, "models_timed": limit,
+                           "packets_per_s": sum(n[:limit]) * n_it / fp64_s if limit else None,
+                           "timing": "host clock around each model's 10 iterations (synchronised)"},
+        "speedup_vs_fp64_per_model": value / fp64_models_s if limit else None,
+        "t_rad_after_10_iterations": {
+            "rms_rel_diff_mixed_vs_fp64": {"median": med(d_mix), "models": limit},
+            "rms_rel_diff_fp64_seed_vs_seed": {"median": med(d_seed), "models": n_noise},
+            "note": "per model, RMS over shells of the relative T_R difference; mixed and binary64 "
+                    "share the seeds, but their histories part after rounding differences, so the "
+                    "comparison is with the seed-to-seed Monte Carlo spread"},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson arrivals of batched-workload models, continuous batching."""
+    import torch
+    from paper_1401_5469_gb300 import mc, serve, synth
+    torch.cuda.set_device(0)
+    mixed = args.precision == "mixed"
+    prec = mc.MC_PRECISION_MIXED if mixed else mc.MC_PRECISION_FP64
+    warm_s, window_s = 10.0, 60.0
+    t0 = time.perf_counter()
+    pool = synth.batched_models(n_models=256, seed=1401)
+    _log(f"generated the model pool in {time.perf_counter() - t0:.1f} s")
+    rng = np.random.default_rng(50)
+    arrivals = []
+    t = 0.0
+    while True:
+        t += float(rng.exponential(1.0 / args.rate))
+        if t >= warm_s + window_s:
+            break
+        arrivals.append(t)
+    reqs = [serve.Request(rid=k, spec=pool[int(rng.integers(len(pool)))],
+                          n_iterations=int(rng.integers(5, 21)), seed=5469 + k, arrival=a)
+            for k, a in enumerate(arrivals)]
+    tick_packets = args.tick_packets or (25_000_000 if mixed else 5_000_000)
+    server = serve.Server(hbm_budget_bytes=150e9, j_blue=False, precision=prec,
+                          max_tick_packets=tick_packets)
+    clocks = ClockSampler(0)
+    clocks.start()
+    start = time.perf_counter()
+    nxt = 0
+    peak_resident = 0
+    while True:
+        now = time.perf_counter() - start
+        if now >= warm_s + window_s:
+            break
+        while nxt < len(reqs) and reqs[nxt].arrival <= now:
+            server.submit(reqs[nxt])
+            nxt += 1
+        if not server.active and not server.queue:
+            if nxt >= len(reqs):
+                break
+            time.sleep(max(0.0, min(reqs[nxt].arrival - now, 0.05)))
+            continue
+        server.step(now)
+        peak_resident = max(peak_resident, len(server.active))
+    end = time.perf_counter() - start
+    clk = clocks.stop()
+    backlog_queued, backlog_active = len(server.queue), len(server.active)
+    server.close()
+    done = [r for r in reqs if r.finished is not None and r.finished <= warm_s + window_s
+            and r.arrival >= warm_s]
+    # requests retired by close() at the end are not finished work
+    done = [r for r in done if r.done_iterations >= r.n_iterations]
+    lat = serve.percentiles([r.latency for r in done])
+    in_window = [r for r in reqs if r.arrival >= warm_s]
+    offered = sum(r.spec.n_packets * r.n_iterations for r in in_window) / window_s
+    served = sum(r.spec.n_packets * r.n_iterations for r in done) / window_s
+    value = len(done) / window_s
+    line = {
+        "metric": "models/s", "value": value, "unit": "models/s", "n_gpus": 1,
+        "steps": server.ticks, "warmup": 0, "ms_per_step": float(np.mean(server.tick_ms)) if server.tick_ms else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"serve-poisson-{args.rate:g}-per-s-{args.precision}",
+                   "arrival_rate": args.rate, "window_s": window_s, "warmup_s": warm_s,
+                   "iterations": [5, 20], "hbm_budget_bytes": 150e9, "max_tick_packets": tick_packets,
+                   "model_pool": "256 batched-workload models (seed 1401), one drawn per request",
+                   "j_blue": False},
+        "latency_s": lat,
+        "requests": {"arrived_in_window": len(in_window), "finished_in_window": len(done),
+                     "backlog_at_end": {"queued": backlog_queued, "resident": backlog_active}},
+        "packet_iterations_per_s": {"offered": offered, "served": served},
+        "ticks": server.ticks, "peak_resident_models": peak_resident,
+        "tick_ms": {"p50": float(np.percentile(server.tick_ms, 50)) if server.tick_ms else None,
+                    "max": float(np.max(server.tick_ms)) if server.tick_ms else None},
+        "elapsed_s": end, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="downbranch", choices=["downbranch", "batched", "serve"])
+    ap.add_argument("--models", type=int, default=256)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--tick-packets", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

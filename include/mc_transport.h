@@ -186,7 +186,8 @@ mc_status mc_run_iteration_range(mc_model *m, uint64_t seed, uint32_t iteration,
 /* Update T_R and W from the last run's estimators (Eqs. 15-16) on the device;
  * shells with no path length keep their values.  The next run recomputes the
  * Sobolev depths when they are not given.  Copies the new values to t_rad_out
- * and w_out ([S], either may be NULL).  Synchronises the stream.
+ * and w_out ([S], either may be NULL); synchronises the stream when either is
+ * given, and is asynchronous on the model's stream when both are NULL.
  *  Errors: MC_ERR_NOT_READY (no run yet), MC_ERR_CUDA. */
 mc_status mc_update_radiation_field(mc_model *m, double *t_rad_out, double *w_out);
 
@@ -232,6 +233,27 @@ mc_status mc_read_transport_phases(mc_model *m, float *ms);
 /* Number of kernels this model has launched since creation. */
 mc_status mc_launch_count(const mc_model *m, uint64_t *count);
 
+/* Device views of the model's estimator buffers, for callers that combine
+ * the partial sums of several packet ranges in place (a sum all-reduce across
+ * processes, one GPU each, each having run mc_run_iteration_range on its own
+ * disjoint range of the same iteration) before mc_update_radiation_field,
+ * which reads j_est and nu_bar from these same buffers (Eqs. 15-16).  Packet
+ * draws are keyed by packet index, so the combined sums are those of the
+ * whole iteration run on one GPU, up to summation order.
+ *  out->j_est, nu_bar: [n_shells] binary64 raw sums (Eqs. 13-14);
+ *  out->j_blue: [n_shells * n_lines] or NULL when J_blue is off;
+ *  out->spectrum: [spec_bins + 2] (last two: below / above the range);
+ *  out->stream: the model's stream (cudaStream_t); the buffers hold the last
+ *  iteration's sums once the work queued there has completed.
+ * The pointers are owned by the model and valid until mc_model_destroy; they
+ * are device memory on the model's device.  Errors: MC_ERR_INVALID_ARG. */
+typedef struct {
+  double *j_est, *nu_bar, *j_blue, *spectrum;
+  uint32_t n_shells, n_lines, spec_bins;
+  void *stream;
+} mc_estimator_views;
+mc_status mc_device_estimators(mc_model *m, mc_estimator_views *out);
+
 /* Wait for the model's stream. */
 mc_status mc_synchronize(mc_model *m);
 
@@ -244,9 +266,12 @@ void mc_model_destroy(mc_model *m);
  * A batch advances several mixed-precision models (MC_PRECISION_MIXED, one
  * device, the same line mode, J_blue and record settings) by one
  * Monte Carlo iteration each with a single persistent transport launch: the
- * packets of all models are drawn from one queue, largest model first.  Each
- * model's iteration is exactly its single-model iteration (same draws, same
- * arithmetic; only the estimator summation order differs).  The whole
+ * packets of all models are drawn from one queue (largest model first by
+ * default).  Each model's iteration is exactly its single-model iteration:
+ * the same draws, the same compiled kernel, and J and nu_bar summed in fixed
+ * point, so J, nu_bar and the updated T_R, W are bit-identical to the model
+ * run alone; only the binary64 J_blue and spectrum sums depend on summation
+ * order.  The whole
  * iteration -- Sobolev depths where stale, estimator zeroing, transport and,
  * when `update` is set, Eqs. 15-16 for every model -- is captured as one CUDA
  * graph on the first call and replayed while the batch's shape (models with
@@ -269,6 +294,41 @@ mc_status mc_batch_synchronize(mc_batch *b);
 mc_status mc_batch_read_timing(mc_batch *b, float *ms);
 const char *mc_batch_last_error_message(const mc_batch *b);
 void mc_batch_destroy(mc_batch *b);
+
+/* Launch shape of a batch.  None of these changes any model's results (the
+ * packet histories and fixed-point J, nu_bar sums do not depend on which
+ * thread transports a packet or when).
+ *  block:         threads per block, 64, 128 or 256 (0: 128).
+ *  blocks_per_sm: resident blocks per SM of the persistent grid (0: as many
+ *                 as fit; larger values are clamped to what fits).
+ *  order:         MC_ORDER_PACKETS -- models with more packets are queued
+ *                 first; MC_ORDER_WORK -- by packets x lines; MC_ORDER_GIVEN --
+ *                 the order passed to mc_batch_create. */
+enum { MC_ORDER_PACKETS = 0, MC_ORDER_WORK = 1, MC_ORDER_GIVEN = 2 };
+typedef struct {
+  uint32_t block;
+  uint32_t blocks_per_sm;
+  uint32_t order;
+} mc_batch_launch;
+
+/* Set the launch shape (MC_ERR_INVALID_ARG for an unknown block size or
+ * order); the next iteration recaptures the graph. */
+mc_status mc_batch_set_launch(mc_batch *b, const mc_batch_launch *launch);
+/* The launch shape in use, with blocks_per_sm resolved to the value used. */
+mc_status mc_batch_get_launch(const mc_batch *b, mc_batch_launch *launch);
+
+/* Autotuner: pick the fastest launch shape for these iterations by timing
+ * transport-only trial iterations (update = 0, the same arguments as
+ * mc_batch_run_iteration).  Coordinate search: queue order, then block size,
+ * then resident blocks per SM, each trial one full batched transport launch
+ * timed with events on the batch stream.  Trials leave every model's T_R, W
+ * and Sobolev depths as they were (the estimators and spectrum hold the last
+ * trial's sums until the next iteration overwrites them).  On return the best
+ * shape is set; `best` and `best_ms` (either may be NULL) receive it and its
+ * transport time; `n_trials` (may be NULL) the number of trials run. */
+mc_status mc_batch_autotune(mc_batch *b, const uint64_t *seeds, const uint32_t *iterations,
+                            const uint64_t *n_packets, const double *t_inner,
+                            mc_batch_launch *best, float *best_ms, uint32_t *n_trials);
 
 /* ---------------------------------------------------------------------------
  * Transport without any allocation.

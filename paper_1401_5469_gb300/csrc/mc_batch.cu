@@ -29,6 +29,9 @@ struct mc_batch {
   std::vector<cudaStream_t> user;  // the models' distinct streams
   int line_mode = 0;
   bool j_blue = false, record = false;
+  int nsm = 1;
+  int max_bps[3] = {0, 0, 0};      // resident blocks per SM at 64, 128, 256 threads
+  uint32_t block = 128, bps_req = 0, order_policy = MC_ORDER_PACKETS;
   int grid = 0;
   TransportParams *d_params = nullptr, *h_params = nullptr;  // device table, pinned host staging
   unsigned long long *d_prefix = nullptr, *h_prefix = nullptr;
@@ -58,6 +61,19 @@ mc_status bcuda(mc_batch *b, cudaError_t e, const char *what) {
   return bfail(b, MC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+int block_slot(uint32_t block) { return block == 64 ? 0 : block == 128 ? 1 : block == 256 ? 2 : -1; }
+
+// Resident blocks per SM used for the current block size.
+int resolved_bps(const mc_batch *b) {
+  const int most = b->max_bps[block_slot(b->block)];
+  return b->bps_req == 0 ? most : std::min<int>(most, static_cast<int>(b->bps_req));
+}
+
+void drop_graph(mc_batch *b) {
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+}
+
 // Enqueue one iteration of every model on the batch stream.
 mc_status enqueue_iteration(mc_batch *b, int update) {
   for (mc_model *m : b->models) {
@@ -77,7 +93,8 @@ mc_status enqueue_iteration(mc_batch *b, int update) {
   p.work_counter = b->d_counters;
   p.flags = b->d_counters + 1;
   e = cudaEventRecordWithFlags(b->t0, b->stream, cudaEventRecordExternal);
-  if (e == cudaSuccess) e = launch_transport_batch(p, b->line_mode, b->j_blue, b->record, b->grid, b->stream);
+  if (e == cudaSuccess) e = launch_transport_batch(p, b->line_mode, b->j_blue, b->record, b->grid,
+                                                    static_cast<int>(b->block), b->stream);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->t1, b->stream, cudaEventRecordExternal);
   if (e != cudaSuccess) return bcuda(b, e, "batched transport");
   b->launches += 1;
@@ -137,14 +154,16 @@ mc_status mc_batch_create(mc_model *const *models, uint32_t n_models, mc_batch *
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreate(&b->t0);
   if (e == cudaSuccess) e = cudaEventCreate(&b->t1);
-  int bps = 0, nsm = 1;
-  if (e == cudaSuccess) e = batch_occupancy(b->line_mode, b->j_blue, b->record, static_cast<int>(n_models), &bps);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m0->device);
-  if (e != cudaSuccess || bps <= 0) {
+  const int blocks[3] = {64, 128, 256};
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+    e = batch_occupancy(b->line_mode, b->j_blue, b->record, static_cast<int>(n_models), blocks[k],
+                        &b->max_bps[k]);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, m0->device);
+  if (e != cudaSuccess || b->max_bps[0] <= 0 || b->max_bps[1] <= 0 || b->max_bps[2] <= 0) {
     mc_batch_destroy(b);
     return bfail(nullptr, MC_ERR_CUDA, std::string("batch create: ") + cudaGetErrorString(e));
   }
-  b->grid = nsm * bps;
+  b->grid = b->nsm * resolved_bps(b);
   for (mc_model *m : b->models) m->in_batch = true;
   *out = b;
   return MC_OK;
@@ -160,15 +179,26 @@ mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, const uint3
     const cudaError_t ew = cudaEventSynchronize(b->t0);
     if (ew != cudaSuccess) return bcuda(b, ew, "previous iteration");
   }
-  // launch order: largest packet count first, so the longest walks start first
+  // queue order (MC_ORDER_PACKETS by default: largest packet count first, so
+  // the longest walks start first)
   std::vector<uint32_t> order(n);
   std::iota(order.begin(), order.end(), 0u);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](uint32_t a, uint32_t c) { return n_packets[a] > n_packets[c]; });
+  std::vector<mc_model *> by_caller(n);
+  for (size_t k = 0; k < n; ++k)
+    by_caller[b->order[k]] = b->models[k];
+  if (b->order_policy == MC_ORDER_PACKETS) {
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t c) { return n_packets[a] > n_packets[c]; });
+  } else if (b->order_policy == MC_ORDER_WORK) {
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) {
+      return static_cast<double>(n_packets[a]) * by_caller[a]->L >
+             static_cast<double>(n_packets[c]) * by_caller[c]->L;
+    });
+  }
   std::vector<mc_model *> launch_models(n);
   for (size_t k = 0; k < n; ++k) {
     const uint32_t i = order[k];
-    mc_model *m = b->models[std::find(b->order.begin(), b->order.end(), i) - b->order.begin()];
+    mc_model *m = by_caller[i];
     launch_models[k] = m;
     if (!m->plasma_set) return bfail(b, MC_ERR_NOT_READY, "a model has no plasma state");
     if (n_packets[i] == 0 || n_packets[i] >= (1ull << 32))
@@ -206,8 +236,7 @@ mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, const uint3
                      b->graph_update == (update != 0) &&
                      b->graph_total == b->h_prefix[n];
   if (!reuse) {
-    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    drop_graph(b);
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bcuda(b, e, "begin capture");
     const mc_status rc = enqueue_iteration(b, update);
@@ -265,12 +294,79 @@ mc_status mc_batch_read_timing(mc_batch *b, float *ms) {
 
 const char *mc_batch_last_error_message(const mc_batch *b) { return b ? b->err.c_str() : ""; }
 
+mc_status mc_batch_set_launch(mc_batch *b, const mc_batch_launch *launch) {
+  if (!b || !launch) return MC_ERR_INVALID_ARG;
+  const uint32_t block = launch->block == 0 ? 128u : launch->block;
+  if (block_slot(block) < 0) return bfail(b, MC_ERR_INVALID_ARG, "block must be 64, 128 or 256");
+  if (launch->order > MC_ORDER_GIVEN) return bfail(b, MC_ERR_INVALID_ARG, "unknown queue order");
+  if (b->graph_launches) {  // the graph in flight reads the parameter table
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "set launch");
+  }
+  b->block = block;
+  b->bps_req = launch->blocks_per_sm;
+  b->order_policy = launch->order;
+  b->grid = b->nsm * resolved_bps(b);
+  drop_graph(b);
+  return MC_OK;
+}
+
+mc_status mc_batch_get_launch(const mc_batch *b, mc_batch_launch *launch) {
+  if (!b || !launch) return MC_ERR_INVALID_ARG;
+  launch->block = b->block;
+  launch->blocks_per_sm = static_cast<uint32_t>(resolved_bps(b));
+  launch->order = b->order_policy;
+  return MC_OK;
+}
+
+mc_status mc_batch_autotune(mc_batch *b, const uint64_t *seeds, const uint32_t *iterations,
+                            const uint64_t *n_packets, const double *t_inner,
+                            mc_batch_launch *best, float *best_ms, uint32_t *n_trials) {
+  if (!b) return MC_ERR_INVALID_ARG;
+  uint32_t trials = 0;
+  // one transport-only iteration with shape c; its device time in *ms
+  auto trial = [&](const mc_batch_launch &c, float *ms) -> mc_status {
+    mc_status rc = mc_batch_set_launch(b, &c);
+    if (rc == MC_OK) rc = mc_batch_run_iteration(b, seeds, iterations, n_packets, t_inner, 0);
+    if (rc == MC_OK) rc = mc_batch_read_timing(b, ms);
+    ++trials;
+    return rc;
+  };
+  mc_batch_launch cur{b->block, 0u, b->order_policy};
+  float cur_ms = 0.0f;
+  // the first trial also absorbs one-time costs (stale Sobolev depths, first
+  // capture); time the starting shape again so that it competes fairly
+  mc_status rc = trial(cur, &cur_ms);
+  if (rc == MC_OK) rc = trial(cur, &cur_ms);
+  auto consider = [&](const mc_batch_launch &c) -> mc_status {
+    float ms = 0.0f;
+    const mc_status r = trial(c, &ms);
+    if (r == MC_OK && ms < cur_ms) { cur = c; cur_ms = ms; }
+    return r;
+  };
+  for (uint32_t o = MC_ORDER_PACKETS; o <= MC_ORDER_WORK && rc == MC_OK; ++o)
+    if (o != cur.order) rc = consider(mc_batch_launch{cur.block, cur.blocks_per_sm, o});
+  const uint32_t blocks[3] = {64u, 128u, 256u};
+  const uint32_t start_block = cur.block;
+  for (uint32_t bl : blocks)
+    if (rc == MC_OK && bl != start_block) rc = consider(mc_batch_launch{bl, 0u, cur.order});
+  const int most = b->max_bps[block_slot(cur.block)];
+  const uint32_t start_bps = cur.blocks_per_sm;
+  for (int k = 1; k < most && rc == MC_OK; ++k)  // 0 (= most) was timed above
+    if (static_cast<uint32_t>(k) != start_bps) rc = consider(mc_batch_launch{cur.block, static_cast<uint32_t>(k), cur.order});
+  if (rc == MC_OK) rc = mc_batch_set_launch(b, &cur);
+  if (rc != MC_OK) return rc;
+  if (best) mc_batch_get_launch(b, best);
+  if (best_ms) *best_ms = cur_ms;
+  if (n_trials) *n_trials = trials;
+  return MC_OK;
+}
+
 void mc_batch_destroy(mc_batch *b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (mc_model *m : b->models) m->in_batch = false;
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
+  drop_graph(b);
   if (b->d_params) cudaFree(b->d_params);
   if (b->d_prefix) cudaFree(b->d_prefix);
   if (b->d_counters) cudaFree(b->d_counters);

@@ -587,11 +587,25 @@ mc_status mc_update_radiation_field(mc_model *m, double *t_rad_out, double *w_ou
   if (!m->have_run) return fail(m, MC_ERR_NOT_READY, "no Monte Carlo run to update from");
   mc_status st = model_update(m, m->stream, true);
   if (st != MC_OK) return st;
+  if (!t_rad_out && !w_out) return MC_OK;  // stays asynchronous on the model's stream
   cudaError_t e = cudaSuccess;
   if (t_rad_out) e = cudaMemcpyAsync(t_rad_out, m->t_rad, m->S * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess && w_out) e = cudaMemcpyAsync(w_out, m->w, m->S * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) return cuda_fail(m, e, "update readout");
+  return MC_OK;
+}
+
+mc_status mc_device_estimators(mc_model *m, mc_estimator_views *out) {
+  if (!m || !out) return MC_ERR_INVALID_ARG;
+  out->j_est = m->j_est;
+  out->nu_bar = m->nu_bar;
+  out->j_blue = m->j_blue;
+  out->spectrum = m->spectrum;
+  out->n_shells = m->S;
+  out->n_lines = m->L;
+  out->spec_bins = m->run.spec_bins;
+  out->stream = m->stream;
   return MC_OK;
 }
 

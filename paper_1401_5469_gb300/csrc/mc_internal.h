@@ -98,6 +98,7 @@ constexpr int kNCounterSlots = kNStats + 5;  // stats, work counter, flags[4]
 // then the same whatever the launch mixes).  Headroom: 2^64 / 2^32 = 4.3e9
 // units per shell.
 constexpr double kEstFixScale = 0x1.0p32;
+constexpr float kEstFixScaleF = 0x1.0p32f;
 
 struct PlasmaParams {
   int32_t S, I, K, L;
@@ -129,9 +130,11 @@ int transport_block_size();
 cudaError_t transport_occupancy(int line_mode, int precision, bool j_blue, bool record, int S,
                                 int *blocks_per_sm);
 const void *select_mixed_kernel(int line_mode, bool j_blue, bool record);
-cudaError_t batch_occupancy(int line_mode, bool j_blue, bool record, int n_models, int *blocks_per_sm);
+// Batched launches: `block` threads per block (64, 128 or 256).
+cudaError_t batch_occupancy(int line_mode, bool j_blue, bool record, int n_models, int block,
+                            int *blocks_per_sm);
 cudaError_t launch_transport_batch(const TransportParams &p, int line_mode, bool j_blue, bool record,
-                                   int grid, cudaStream_t st);
+                                   int grid, int block, cudaStream_t st);
 size_t mixed_smem_bytes(int S);
 cudaError_t launch_to_f32(const double *in, float *out, size_t n, cudaStream_t st);
 // j_est = fix[s] 2^-32 E, nu_bar = fix[S + s] 2^-32 E nu_ref (mixed precision).

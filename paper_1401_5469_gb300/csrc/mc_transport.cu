@@ -8,9 +8,10 @@
 // its longest random walks (the packet queue empties within a few percent of
 // the kernel time), so the kernel minimises binary64 instructions per flight
 // segment:
-//  * the packet carries p = x mu, q = x^2 - p^2 (conserved in free flight) and
-//    x^2 (radii in units of c t_exp): D = 1 - p, the shell distance needs one
-//    root, and a shell crossing is p += l;
+//  * the packet carries p = x mu and q = x^2 - p^2 (conserved in free flight;
+//    radii in units of c t_exp): D = 1 - p, x^2 = q + p^2, the shell exit is
+//    at p = +-sqrt(x_b^2 - q) -- a root taken only when a line is passed or
+//    the shell event wins -- and a flight of length l is p += l;
 //  * the line scan runs in the frequency domain: a Sobolev point is the
 //    closest event while nu_line > max(nu_shell, nu_e), where nu_shell and
 //    nu_e are the comoving frequencies reached at d_shell and d_e; passing a
@@ -39,7 +40,7 @@ constexpr int kShellArrays = 6;  // x_in^2, x_out^2, x_in, x_out, kappa, 1/kappa
 constexpr int kLineEvent = 1, kElectronEvent = 2, kShellEvent = 3;
 
 struct Packet {
-  double p, q, r2;           // x mu, x^2 - p^2, x^2
+  double p, q;               // x mu, x^2 - p^2
   double nu_lab, e_lab, inv_nu, inv_D;
   int32_t shell, next_line;
   uint32_t pid;
@@ -111,6 +112,25 @@ __device__ __forceinline__ Emission downbranch_pick(const TransportParams &p, in
 // max(v, 0) through the integer keys (no binary64 instruction).
 __device__ __forceinline__ double max0(double v) { return okey(v) > 0 ? v : 0.0; }
 
+// x mu at the shell exit: +sqrt(x_out^2 - q), or -sqrt(x_in^2 - q) when the
+// ray meets the inner sphere.
+__device__ __forceinline__ double shell_exit(double q, bool inner, double xi2, double xo2) {
+  const double root = sqrt((inner ? xi2 : xo2) - q);
+  return inner ? -root : root;
+}
+
+// Does an event at path length l (units of c t_exp) come before the shell
+// exit?  Along the ray x mu grows by l and x^2 = q + (x mu)^2.  Outward exit:
+// before it exactly when x^2 < x_out^2 there (a point with x mu < 0 has
+// x^2 <= the current x^2).  Inner exit at x mu = -sqrt(x_in^2 - q): before
+// it exactly when x mu < 0 and x^2 > x_in^2 there.
+__device__ __forceinline__ bool inside_shell(double pp, double q, double l, bool inner, double xi2,
+                                             double xo2) {
+  const double pl = pp + l;
+  const long long k2 = okey(fma(pl, pl, q));
+  return inner ? (okey(pl) < -1 && k2 > okey(xi2)) : k2 < okey(xo2);
+}
+
 // Injection at the inner boundary, Sect. 2.4: Planck-sampled comoving
 // frequency (Carter & Cashwell series method), mu = sqrt(z), equal comoving
 // energy (Eq. 10), lab-frame values by the first-order Doppler factor.
@@ -128,7 +148,6 @@ __device__ __forceinline__ void inject(const TransportParams &p, const double *p
   const double D = 1.0 - pp;
   const double iD = rcp64(D);
   pk.p = pp;
-  pk.r2 = x0sq;
   pk.q = max0(fma(-pp, pp, x0sq));
   pk.nu_lab = nu_cmf * iD;
   pk.e_lab = p.e_cmf * iD;
@@ -215,7 +234,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
     } else {
       pk.cnt[0] += 1u;
       const int32_t s = pk.shell;
-      const double pp = pk.p, q = pk.q, r2 = pk.r2, nu_lab = pk.nu_lab, inv_nu = pk.inv_nu;
+      const double pp = pk.p, q = pk.q, nu_lab = pk.nu_lab, inv_nu = pk.inv_nu;
       // Doppler factor D = 1 - mu v/c, comoving frequency (Sect. 2.5)
       const double D = 1.0 - pp;
       const double inv_D = pk.have_inv_D ? pk.inv_D : rcp64(D);
@@ -230,9 +249,14 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       // length is p_exit - p and the comoving frequency there nu_lab (1 - p_exit).
       const double xi2 = s_xi2[s], xo2 = s_xo2[s];
       const bool inner = okey(pp) < -1 && okey(q) <= okey(xi2);  // p < 0 (not -0)
-      const double root = sqrt((inner ? xi2 : xo2) - q);
-      const double p_exit = inner ? -root : root;
-      const long long key_shell = okey(nu_lab * (1.0 - p_exit));
+      // The root (one binary64 square root, ~650 cycles) is taken only when
+      // a line is passed or the shell event wins: an event at path length l
+      // lies inside the shell exactly when the radius there, x^2 = q + (p+l)^2,
+      // has not reached the exit sphere -- the same p + l and x^2 the move
+      // to the event computes anyway.
+      double p_exit = 0.0;
+      long long key_shell = kKeyNegInf;
+      bool have_shell = false;
       double c_e = 0.0, thr_e = 0.0;
       long long key_e = kKeyNegInf;
       if (thomson) {
@@ -240,7 +264,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         thr_e = fma(-tau_rem, c_e, nu_cmf);
         key_e = okey(thr_e);
       }
-      long long key_thr = key_shell > key_e ? key_shell : key_e;
+      long long key_thr = key_e;  // the shell threshold joins once known
       const double e_inv2 = JB ? (pk.e_lab * inv_nu) * inv_nu : 0.0;
       const size_t row = static_cast<size_t>(s) * static_cast<size_t>(L);
       const double *tau_s = p.tau + row;
@@ -272,37 +296,59 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
           tau_nn = __ldg(tau_s + j + 2);
           if (MODE == 1 && p.row_info) rinfo_nn = __ldg(p.row_info + j + 2);
         }
-        if (bj <= key_thr) break;  // the Sobolev point lies beyond d_shell or d_e
-        pk.cnt[2] += 1u;
+        if (bj <= key_thr) break;  // the Sobolev point lies beyond d_e (or the shell exit)
         const double nuj = __longlong_as_double(bj);
-        if (JB) atomicAdd(p.j_blue + row + j, nuj * e_inv2);
         bool absorbed;
+        double t = 0.0;
         if (thomson) {
-          const double t = fma(taul, c_e, thr_e);
+          t = fma(taul, c_e, thr_e);
           absorbed = okey(t) > bj;
-          if (!absorbed) {
-            thr_e = t;
-            key_e = okey(t);
-            key_thr = key_shell > key_e ? key_shell : key_e;
-          }
         } else {
           absorbed = okey(taul) > okey(tau_rem);
-          if (!absorbed) tau_rem -= taul;
         }
         if (absorbed) {
+          const double lj = max0(fma(-nuj, inv_nu, D));
+          if (!have_shell && !inside_shell(pp, q, lj, inner, xi2, xo2)) break;  // exit comes first
+          pk.cnt[2] += 1u;
+          if (JB) atomicAdd(p.j_blue + row + j, nuj * e_inv2);
           kind = kLineEvent;
-          l = max0(fma(-nuj, inv_nu, D));
+          l = lj;
           nu_hit = nuj;
           rinfo_hit = rinfo;
           break;
+        }
+        if (!have_shell) {  // a line is passed: the scan needs the exit threshold
+          p_exit = shell_exit(q, inner, xi2, xo2);
+          key_shell = okey(nu_lab * (1.0 - p_exit));
+          have_shell = true;
+          key_thr = key_shell > key_e ? key_shell : key_e;
+          if (bj <= key_shell) break;  // this line lies beyond the exit
+        }
+        pk.cnt[2] += 1u;
+        if (JB) atomicAdd(p.j_blue + row + j, nuj * e_inv2);
+        if (thomson) {
+          thr_e = t;
+          key_e = okey(t);
+          key_thr = key_shell > key_e ? key_shell : key_e;
+        } else {
+          tau_rem -= taul;
         }
         ++j;
         bj = bj_n; taul = tau_n; rinfo = rinfo_n;
         bj_n = bj_nn; tau_n = tau_nn; rinfo_n = rinfo_nn;
       }
       if (kind == 0) {
-        if (key_e > key_shell) { kind = kElectronEvent; l = max0(fma(-thr_e, inv_nu, D)); }
-        else { kind = kShellEvent; l = max0(p_exit - pp); }
+        const double le = thomson ? max0(fma(-thr_e, inv_nu, D)) : 0.0;
+        const bool electron = have_shell ? key_e > key_shell
+                                         : thomson && inside_shell(pp, q, le, inner, xi2, xo2);
+        if (electron) {
+          kind = kElectronEvent;
+          l = le;
+        } else {
+          if (!have_shell) p_exit = shell_exit(q, inner, xi2, xo2);
+          kind = kShellEvent;
+          l = max0(p_exit - pp);
+        }
       }
       // estimators, Eqs. 13-14 (segment-start comoving values)
       const double wgt = eD2 * l;
@@ -321,7 +367,6 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         pk.cnt[5] += 1u;
         const int32_t ns = inner ? s - 1 : s + 1;
         pk.p = p_exit;
-        pk.r2 = inner ? xi2 : xo2;
         pk.shell = ns;
         pk.have_inv_D = false;
         if (ns >= S) status = 1;
@@ -358,7 +403,6 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         const double iD2 = rcp64(D2);
         pk.p = pn;
         pk.q = max0(fma(-pn, pn, r2n));
-        pk.r2 = r2n;
         pk.nu_lab = nu_c * iD2;
         pk.e_lab = e_c * iD2;
         pk.inv_nu = inv_nu_c * D2;

@@ -27,7 +27,8 @@ namespace mcgpu {
 
 namespace {
 
-constexpr int kBlock = 128;
+// single-model launches take 128 threads per block, batched ones 64, 128 or 256
+constexpr int kMaxBlock = 256;
 constexpr int kLineEvent = 1, kElectronEvent = 2, kShellEvent = 3;
 
 struct PacketM {
@@ -50,7 +51,7 @@ struct MCtx {
   double *j_blue, *j_est, *nu_bar, *spectrum;
   unsigned long long *stats;
   unsigned long long *est_fix;  // [2 S] J, nu_bar in fixed point
-  double inv_nu_ref;
+  float inv_nu_ref;
   const double *planck;
   int32_t S, L, spec_bins;
   uint32_t key0, key1, iteration;
@@ -80,7 +81,7 @@ __device__ __forceinline__ void load_ctx(MCtx &c, const TransportParams &q, cons
   c.spectrum = q.spectrum;
   c.stats = q.stats;
   c.est_fix = q.est_fix;
-  c.inv_nu_ref = q.inv_nu_ref;
+  c.inv_nu_ref = static_cast<float>(q.inv_nu_ref);
   c.planck = q.planck_cdf;
   c.spec_bins = q.spec_bins;
   c.key0 = q.key0;
@@ -135,6 +136,23 @@ __device__ __forceinline__ void pick_m(const MCtx &c, unsigned long long rinfo, 
 
 __device__ __forceinline__ float max0f(float v) { return v > 0.0f ? v : 0.0f; }
 
+// x mu at the shell exit, +sqrt(x_out^2 - q) or -sqrt(x_in^2 - q).
+__device__ __forceinline__ float shell_exit_f(float q, bool inner, float xi2, float xo2) {
+  const float root = sqrtf(max0f((inner ? xi2 : xo2) - q));
+  return inner ? -root : root;
+}
+
+// Does an event at path length l come before the shell exit?  x mu grows by
+// l along the ray and x^2 = q + (x mu)^2: before an outward exit exactly when
+// x^2 < x_out^2 there; before an inner exit exactly when x mu < 0 and
+// x^2 > x_in^2 there.
+__device__ __forceinline__ bool inside_shell_f(float pp, float q, float l, bool inner, float xi2,
+                                               float xo2) {
+  const float pl = pp + l;
+  const float r2 = fmaf(pl, pl, q);
+  return inner ? (pl < 0.0f && r2 > xi2) : r2 < xo2;
+}
+
 // uniform in (0, 1] with 24 random bits
 __device__ __forceinline__ float open0f(unsigned long long u53) {
   return static_cast<float>((u53 >> 29) + 1ull) * 0x1.0p-24f;
@@ -156,7 +174,7 @@ __device__ __forceinline__ void flush_stats(Stats &st, unsigned long long *dst) 
 // launches run the same machine code, so a model's results do not depend on
 // the company it is launched in.
 template <int MODE, bool JB, bool REC>
-__global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams p) {
+__global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportParams p) {
   extern __shared__ unsigned long long smem_u64[];
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lanemask_lt = (1u << lane) - 1u;
@@ -280,9 +298,11 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
       const float tau0 = -__logf(open0f(ds.next_u53()));
       const float xi2 = c.xi2[s], xo2 = c.xo2[s];
       const bool inner = pp < 0.0f && q <= xi2;
-      const float root = sqrtf(max0f((inner ? xi2 : xo2) - q));
-      const float p_exit = inner ? -root : root;
-      const long long key_shell = okey(nu_lab * static_cast<double>(1.0f - p_exit));
+      // shell exit threshold only once a line is passed or the exit wins
+      // (see inside_shell_f)
+      float p_exit = 0.0f;
+      long long key_shell = kKeyNegInf;
+      bool have_shell = false;
       float c_e = 0.0f, tau_rem = tau0;
       double thr_e = 0.0;
       long long key_e = kKeyNegInf;
@@ -291,7 +311,7 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         thr_e = nu_cmf - static_cast<double>(tau0 * c_e);
         key_e = okey(thr_e);
       }
-      long long key_thr = key_shell > key_e ? key_shell : key_e;
+      long long key_thr = key_e;
       const float e_inv2 = JB ? (pk.e_lab * inv_nu) * inv_nu : 0.0f;
       const size_t row = static_cast<size_t>(s) * static_cast<size_t>(L);
       const float *tau_s = c.tau32 + row;
@@ -325,25 +345,39 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
           if (MODE == 1) rinfo_nn = __ldg(c.row_info + j + 2);
         }
         if (bj <= key_thr) break;
-        pk.cnt[2] += 1u;
         const double nuj = __longlong_as_double(bj);
-        if (JB) atomicAdd(c.j_blue + row + j, static_cast<double>(static_cast<float>(nuj) * e_inv2) * c.e_cmf);
         bool absorbed;
+        double t = 0.0;
         if (thomson) {
-          const double t = thr_e + static_cast<double>(taul * c_e);
+          t = thr_e + static_cast<double>(taul * c_e);
           absorbed = okey(t) > bj;
-          if (!absorbed) {
+        } else {
+          absorbed = taul > tau_rem;
+        }
+        if (!absorbed) {
+          if (!have_shell) {  // a line is passed: the scan needs the exit threshold
+            p_exit = shell_exit_f(q, inner, xi2, xo2);
+            key_shell = okey(nu_lab * static_cast<double>(1.0f - p_exit));
+            have_shell = true;
+            key_thr = key_shell > key_e ? key_shell : key_e;
+            if (bj <= key_shell) break;  // this line lies beyond the exit
+          }
+          pk.cnt[2] += 1u;
+          if (JB) atomicAdd(c.j_blue + row + j, static_cast<double>(static_cast<float>(nuj) * e_inv2) * c.e_cmf);
+          if (thomson) {
             thr_e = t;
             key_e = okey(t);
             key_thr = key_shell > key_e ? key_shell : key_e;
+          } else {
+            tau_rem -= taul;
           }
         } else {
-          absorbed = taul > tau_rem;
-          if (!absorbed) tau_rem -= taul;
-        }
-        if (absorbed) {
+          const float lj = max0f(static_cast<float>(nu_cmf - nuj) * inv_nu);
+          if (!have_shell && !inside_shell_f(pp, q, lj, inner, xi2, xo2)) break;  // exit comes first
+          pk.cnt[2] += 1u;
+          if (JB) atomicAdd(c.j_blue + row + j, static_cast<double>(static_cast<float>(nuj) * e_inv2) * c.e_cmf);
           kind = kLineEvent;
-          l = max0f(static_cast<float>(nu_cmf - nuj) * inv_nu);
+          l = lj;
           nu_hit = nuj;
           rinfo_hit = rinfo;
           break;
@@ -353,11 +387,20 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         bj_n = bj_nn; tau_n = tau_nn; rinfo_n = rinfo_nn;
       }
       if (kind == 0) {
-        if (key_e > key_shell) { kind = kElectronEvent; l = max0f(static_cast<float>(nu_cmf - thr_e) * inv_nu); }
-        else { kind = kShellEvent; l = max0f(p_exit - pp); }
+        const float le = thomson ? max0f(static_cast<float>(nu_cmf - thr_e) * inv_nu) : 0.0f;
+        const bool electron = have_shell ? key_e > key_shell
+                                         : thomson && inside_shell_f(pp, q, le, inner, xi2, xo2);
+        if (electron) {
+          kind = kElectronEvent;
+          l = le;
+        } else {
+          if (!have_shell) p_exit = shell_exit_f(q, inner, xi2, xo2);
+          kind = kShellEvent;
+          l = max0f(p_exit - pp);
+        }
       }
       // estimators: binary32 contribution (units of E), summed in fixed point
-      const double wgt = static_cast<double>(eD2 * l);
+      const float wgt = eD2 * l;
       if (s != acc_s) {
         if (acc_s >= 0) {
           atomicAdd(c.est_fix + acc_s, acc_j);
@@ -365,8 +408,10 @@ __global__ void __launch_bounds__(kBlock) transport_mixed(const TransportParams 
         }
         acc_s = s; acc_j = 0ull; acc_nb = 0ull;
       }
-      acc_j += __double2ull_rn(wgt * kEstFixScale);
-      acc_nb += __double2ull_rn((wgt * (nu_cmf * c.inv_nu_ref)) * kEstFixScale);
+      // (x 2^32 is exact; the binary32 to integer conversions do not touch
+      // the binary64 pipe)
+      acc_j += __float2ull_rn(wgt * kEstFixScaleF);
+      acc_nb += __float2ull_rn((wgt * (static_cast<float>(nu_cmf) * c.inv_nu_ref)) * kEstFixScaleF);
       pk.next_line = j;
       if (kind == kShellEvent) {
         pk.cnt[5] += 1u;
@@ -479,16 +524,17 @@ const void *select_mixed_kernel(int line_mode, bool jb, bool rec) { return selec
 
 size_t mixed_smem_bytes(int S) { return 4 * static_cast<size_t>(S) * sizeof(float); }
 
-cudaError_t batch_occupancy(int line_mode, bool j_blue, bool record, int n_models, int *blocks_per_sm) {
+cudaError_t batch_occupancy(int line_mode, bool j_blue, bool record, int n_models, int block,
+                            int *blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, select_b(line_mode, j_blue, record), kBlock,
+      blocks_per_sm, select_b(line_mode, j_blue, record), block,
       static_cast<size_t>(n_models + 1) * sizeof(unsigned long long));
 }
 
 cudaError_t launch_transport_batch(const TransportParams &p, int line_mode, bool j_blue, bool record,
-                                   int grid, cudaStream_t st) {
+                                   int grid, int block, cudaStream_t st) {
   void *args[] = {const_cast<TransportParams *>(&p)};
-  return cudaLaunchKernel(select_b(line_mode, j_blue, record), dim3(grid), dim3(kBlock), args,
+  return cudaLaunchKernel(select_b(line_mode, j_blue, record), dim3(grid), dim3(block), args,
                           static_cast<size_t>(p.n_models + 1) * sizeof(unsigned long long), st);
 }
 

@@ -40,7 +40,11 @@ EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_run_iter
             "mc_read_timing", "mc_read_transport_phases", "mc_launch_count", "mc_synchronize", "mc_model_destroy",
             "mc_status_string", "mc_last_error_message", "mc_transport_noalloc",
             "mc_batch_create", "mc_batch_run_iteration", "mc_batch_synchronize",
-            "mc_batch_read_timing", "mc_batch_last_error_message", "mc_batch_destroy")
+            "mc_batch_read_timing", "mc_batch_last_error_message", "mc_batch_destroy",
+            "mc_batch_set_launch", "mc_batch_get_launch", "mc_batch_autotune",
+            "mc_device_estimators")
+
+MC_ORDER_PACKETS, MC_ORDER_WORK, MC_ORDER_GIVEN = 0, 1, 2
 
 
 class mc_geometry_desc(C.Structure):
@@ -83,6 +87,27 @@ class mc_noalloc_args(C.Structure):
 
 
 MC_NOALLOC_MAX_SHELLS = 1024
+
+
+class mc_estimator_views(C.Structure):
+    _fields_ = [("j_est", C.c_void_p), ("nu_bar", C.c_void_p), ("j_blue", C.c_void_p),
+                ("spectrum", C.c_void_p), ("n_shells", C.c_uint32), ("n_lines", C.c_uint32),
+                ("spec_bins", C.c_uint32), ("stream", C.c_void_p)]
+
+
+class _DeviceArray:
+    """A non-owning device buffer exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f8",
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+class mc_batch_launch(C.Structure):
+    _fields_ = [("block", C.c_uint32), ("blocks_per_sm", C.c_uint32), ("order", C.c_uint32)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -167,6 +192,14 @@ def load(build_if_missing: bool = True):
     L.mc_batch_last_error_message.argtypes = [vp]
     L.mc_batch_destroy.restype = None
     L.mc_batch_destroy.argtypes = [vp]
+    L.mc_device_estimators.restype = i32
+    L.mc_device_estimators.argtypes = [vp, P(mc_estimator_views)]
+    L.mc_batch_set_launch.restype = i32
+    L.mc_batch_set_launch.argtypes = [vp, P(mc_batch_launch)]
+    L.mc_batch_get_launch.restype = i32
+    L.mc_batch_get_launch.argtypes = [vp, P(mc_batch_launch)]
+    L.mc_batch_autotune.restype = i32
+    L.mc_batch_autotune.argtypes = [vp, vp, vp, vp, vp, P(mc_batch_launch), vp, vp]
     _lib = L
     return L
 
@@ -388,6 +421,19 @@ class Model:
         mc_read_estimators(self.h, j, nb, jb, norm)
         return j, nb, jb, norm
 
+    def device_estimators(self):
+        """Torch views (no copy) of the model's device estimator buffers:
+        {"j_est", "nu_bar", "spectrum", "j_blue" (None when off), "stream"}."""
+        import torch
+        v = mc_estimator_views()
+        _check(load().mc_device_estimators(self.h, C.byref(v)), self.h)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        view = lambda ptr, n: torch.as_tensor(_DeviceArray(ptr, n), device=dev)
+        return {"j_est": view(v.j_est, v.n_shells), "nu_bar": view(v.nu_bar, v.n_shells),
+                "spectrum": view(v.spectrum, v.spec_bins + 2),
+                "j_blue": view(v.j_blue, v.n_shells * v.n_lines) if v.j_blue else None,
+                "stream": v.stream}
+
     def spectrum(self):
         sp = np.zeros(self.bins + 2)
         st = mc_packet_stats()
@@ -443,15 +489,38 @@ class Batch:
         msg = load().mc_batch_last_error_message(self.h).decode() or load().mc_status_string(rc).decode()
         raise MCError(rc, msg)
 
-    def run_iteration(self, seeds, iterations, n_packets, t_inner, update=True):
-        """Model i runs its iteration iterations[i] with seeds[i] (scalars broadcast)."""
+    def _args(self, seeds, iterations, n_packets, t_inner):
         n = len(self.models)
         s = np.ascontiguousarray(np.broadcast_to(np.asarray(seeds, dtype=np.uint64), (n,)))
         its = np.ascontiguousarray(np.broadcast_to(np.asarray(iterations, dtype=np.uint32), (n,)))
         npk = np.ascontiguousarray(np.broadcast_to(np.asarray(n_packets, dtype=np.uint64), (n,)))
         t = np.ascontiguousarray(np.broadcast_to(np.asarray(t_inner, dtype=np.float64), (n,)))
+        return s, its, npk, t
+
+    def run_iteration(self, seeds, iterations, n_packets, t_inner, update=True):
+        """Model i runs its iteration iterations[i] with seeds[i] (scalars broadcast)."""
+        s, its, npk, t = self._args(seeds, iterations, n_packets, t_inner)
         return self._bcheck(load().mc_batch_run_iteration(self.h, _p(s), _p(its), _p(npk), _p(t),
                                                           int(bool(update))))
+
+    def set_launch(self, block=0, blocks_per_sm=0, order=MC_ORDER_PACKETS):
+        c = mc_batch_launch(block, blocks_per_sm, order)
+        return self._bcheck(load().mc_batch_set_launch(self.h, C.byref(c)))
+
+    def launch(self):
+        c = mc_batch_launch()
+        self._bcheck(load().mc_batch_get_launch(self.h, C.byref(c)))
+        return c.as_dict()
+
+    def autotune(self, seeds, iterations, n_packets, t_inner):
+        """mc_batch_autotune: returns (launch shape, its transport ms, trials)."""
+        s, its, npk, t = self._args(seeds, iterations, n_packets, t_inner)
+        best = mc_batch_launch()
+        ms = np.zeros(1, dtype=np.float32)
+        nt = np.zeros(1, dtype=np.uint32)
+        self._bcheck(load().mc_batch_autotune(self.h, _p(s), _p(its), _p(npk), _p(t), C.byref(best),
+                                              _p(ms), _p(nt)))
+        return best.as_dict(), float(ms[0]), int(nt[0])
 
     def synchronize(self):
         return self._bcheck(load().mc_batch_synchronize(self.h))

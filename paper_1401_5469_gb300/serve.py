@@ -1,14 +1,19 @@
 """Continuous-batching service for spectral-fit model evaluations.
 
 Each request is one ejecta model to be iterated K times (Sect. 2.8: Sobolev
-depths from T_R and W, Monte Carlo transport, T_R/W update) in mixed
-precision.  The service keeps every admitted model resident on the GPU
-(plasma state, line data and estimators stay in device memory across its
-iterations) and advances all resident models together, one batched transport
-launch (a captured CUDA graph) per tick.  Requests that arrive while others
-are on the GPU are admitted at the next tick if the HBM budget allows, so
+depths from T_R and W, Monte Carlo transport, T_R/W update).  The service
+keeps every admitted model resident on the GPU (plasma state, line data and
+estimators stay in device memory across its iterations) and advances all
+resident models together, one iteration each per tick.  Requests that arrive
+while others are on the GPU are admitted first come, first served at the next
+tick while the HBM budget (and the optional per-tick packet budget) allows, so
 their iterations overlap on the device with the models already running; a
 model leaves as soon as its last iteration is done.
+
+In mixed precision a tick is one batched transport launch for all resident
+models (a captured CUDA graph).  In binary64 a tick launches every resident
+model's own iteration on the model's own stream, so that one model's long
+last random walks overlap the other models' work.
 
 A request's results depend only on its own model, seed and iteration count:
 packet draws are keyed by (seed, iteration, packet), single and batched
@@ -28,13 +33,14 @@ import numpy as np
 from . import mc
 
 
-def model_footprint_bytes(spec, j_blue: Optional[bool] = None) -> int:
-    """Device bytes a mixed-precision model holds (Sobolev depths, J_blue,
-    line list, branching tables, level data, spectrum)."""
+def model_footprint_bytes(spec, j_blue: Optional[bool] = None,
+                          precision: int = mc.MC_PRECISION_MIXED) -> int:
+    """Device bytes a model holds (Sobolev depths, J_blue, line list,
+    branching tables, level data, spectrum)."""
     S, L = spec.n_shells, spec.n_lines
     jb = spec.j_blue if j_blue is None else j_blue
     nnz = L if spec.dbr_line is None else int(spec.dbr_line.shape[0])
-    b = 4 * S * L                      # binary32 Sobolev depths
+    b = (4 if precision == mc.MC_PRECISION_MIXED else 8) * S * L  # Sobolev depths
     b += 8 * S * L if jb else 0        # J_blue sums
     b += L * (8 + 8 + 4 * 3 + 8 + 8)   # nu, f, ion/lower/upper, per-line constants, row info
     b += L * (4 * 3 + 8)               # staged line arrays used at set-up
@@ -70,12 +76,23 @@ class Request:
 
 class Server:
     """Admits requests under an HBM budget and advances all resident models
-    with one batched launch per tick."""
+    by one iteration per tick.
 
-    def __init__(self, hbm_budget_bytes: float = 150e9, j_blue: bool = True, stream=None):
+    hbm_budget_bytes: device bytes the resident models may hold together.
+    max_tick_packets: admit no further request while the resident models'
+        packets per iteration exceed this (None: no limit); bounds the tick
+        length, so that finished models leave and waiting ones enter often.
+    precision: mc.MC_PRECISION_MIXED (batched launch) or MC_PRECISION_FP64.
+    """
+
+    def __init__(self, hbm_budget_bytes: float = 150e9, j_blue: bool = True, stream=None,
+                 precision: int = mc.MC_PRECISION_MIXED, max_tick_packets: Optional[int] = None):
         self.budget = float(hbm_budget_bytes)
         self.j_blue = j_blue
         self.stream = stream
+        self.precision = precision
+        self.max_tick_packets = max_tick_packets
+        self.tick_packets = 0
         self.queue: Deque[Request] = deque()
         self.active: Dict[int, tuple] = {}   # rid -> (request, model, bytes)
         self.used = 0
@@ -93,22 +110,27 @@ class Server:
     def _admit(self, now: float):
         while self.queue:
             req = self.queue[0]
-            need = model_footprint_bytes(req.spec, self.j_blue)
+            need = model_footprint_bytes(req.spec, self.j_blue, self.precision)
             if self.active and self.used + need > self.budget:
                 break
+            if (self.active and self.max_tick_packets is not None
+                    and self.tick_packets + req.spec.n_packets > self.max_tick_packets):
+                break
             self.queue.popleft()
-            m = mc.Model(req.spec, precision=mc.MC_PRECISION_MIXED, j_blue=self.j_blue,
+            m = mc.Model(req.spec, precision=self.precision, j_blue=self.j_blue,
                          stream=self.stream)
             m.set_plasma()
             req.admitted = now
             self.active[req.rid] = (req, m, need)
             self.used += need
+            self.tick_packets += req.spec.n_packets
 
     def _retire(self, rid: int, now: float):
         req, m, need = self.active.pop(rid)
         req.finished = now
         m.close()
         self.used -= need
+        self.tick_packets -= req.spec.n_packets
         self.done.append(req)
 
     # -- one tick: every resident model advances by one iteration
@@ -117,20 +139,30 @@ class Server:
         if not self.active:
             return 0
         ids = sorted(self.active)
-        if ids != self.batch_ids:
-            if self.batch is not None:
-                self.batch.close()
-            self.batch = mc.Batch([self.active[r][1] for r in ids])
-            self.batch_ids = ids
         reqs = [self.active[r][0] for r in ids]
-        t0 = time.perf_counter()
-        # each model runs its own next iteration (draws keyed by its seed and index)
-        self.batch.run_iteration([r.seed for r in reqs], [r.done_iterations for r in reqs],
-                                 [r.spec.n_packets for r in reqs], [r.spec.t_inner for r in reqs],
-                                 update=True)
-        self.batch.synchronize()
-        self.tick_ms.append(1e3 * (time.perf_counter() - t0))
-        self.transport_ms.append(self.batch.transport_ms())
+        if self.precision == mc.MC_PRECISION_MIXED:
+            if ids != self.batch_ids:
+                if self.batch is not None:
+                    self.batch.close()
+                self.batch = mc.Batch([self.active[r][1] for r in ids])
+                self.batch_ids = ids
+            t0 = time.perf_counter()
+            # each model runs its own next iteration (draws keyed by its seed and index)
+            self.batch.run_iteration([r.seed for r in reqs], [r.done_iterations for r in reqs],
+                                     [r.spec.n_packets for r in reqs], [r.spec.t_inner for r in reqs],
+                                     update=True)
+            self.batch.synchronize()
+            self.tick_ms.append(1e3 * (time.perf_counter() - t0))
+            self.transport_ms.append(self.batch.transport_ms())
+        else:
+            t0 = time.perf_counter()
+            models = [self.active[r][1] for r in ids]
+            for r, m in zip(reqs, models):  # asynchronous, one stream per model
+                m.run_iteration(r.seed, r.done_iterations, r.spec.n_packets, r.spec.t_inner)
+                mc.mc_update_radiation_field(m.h, None, None)
+            for m in models:
+                m.synchronize()
+            self.tick_ms.append(1e3 * (time.perf_counter() - t0))
         self.ticks += 1
         finished = []
         for r in reqs:

@@ -78,3 +78,15 @@ def test_create_rejects_invalid_models(mutate, expect):
     assert rc == expect
     assert not h.value
     assert L.mc_last_error_message(None).decode()
+
+
+def test_batch_calls_reject_null_arguments():
+    L = mc.load()
+    c = mc.mc_batch_launch(128, 0, 0)
+    assert L.mc_batch_set_launch(None, C.byref(c)) == mc.MC_ERR_INVALID_ARG
+    assert L.mc_batch_get_launch(None, C.byref(c)) == mc.MC_ERR_INVALID_ARG
+    assert L.mc_batch_autotune(None, None, None, None, None, None, None, None) == mc.MC_ERR_INVALID_ARG
+    assert L.mc_batch_run_iteration(None, None, None, None, None, 1) == mc.MC_ERR_INVALID_ARG
+    h = C.c_void_p()
+    assert L.mc_batch_create(None, 0, C.byref(h)) == mc.MC_ERR_INVALID_ARG
+    assert not h.value

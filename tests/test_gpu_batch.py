@@ -95,3 +95,65 @@ def test_batch_rejects_fp64_models(mc):
         mc.Batch([m])
     assert ei.value.code == mc.MC_ERR_UNSUPPORTED
     m.close()
+
+
+def test_launch_shape_and_autotune_leave_results_unchanged(mc):
+    """Block size, resident blocks per SM and queue order change only which
+    thread carries a packet and when; J, nu_bar, T_R, W stay bit-identical and
+    the packets' fates and frequencies identical.  The autotuner's trials
+    (transport only) leave the models' state as it was."""
+    specs = _specs()
+    seeds = [7 + k for k in range(len(specs))]
+    n = [s.n_packets for s in specs]
+    t_in = [s.t_inner for s in specs]
+    shapes = [None, dict(block=64, blocks_per_sm=1, order=mc.MC_ORDER_GIVEN),
+              dict(block=256, blocks_per_sm=0, order=mc.MC_ORDER_WORK), "autotune"]
+    results = []
+    for shape in shapes:
+        models = [mc.Model(s, precision=mc.MC_PRECISION_MIXED, record_packets=True) for s in specs]
+        for m in models:
+            m.set_plasma()
+        b = mc.Batch(models)
+        if shape == "autotune":
+            best, ms, trials = b.autotune(seeds, 0, n, t_in)
+            assert best["block"] in (64, 128, 256) and best["blocks_per_sm"] >= 1 and ms > 0 and trials >= 4
+            assert b.launch() == best
+        elif shape is not None:
+            b.set_launch(**shape)
+            got = b.launch()
+            assert got["block"] == shape["block"] and got["order"] == shape["order"]
+        out = []
+        for it in range(2):
+            b.run_iteration(seeds, it, n, t_in, update=True)
+            b.synchronize()
+            per = []
+            for k, m in enumerate(models):
+                j, nb, _, _ = m.estimators()
+                t, w, _ = m.plasma()
+                st, nu, e, _ = m.packets(0, n[k])
+                per.append((j, nb, t, w, st, nu, e))
+            out.append(per)
+        b.close()
+        for m in models:
+            m.close()
+        results.append(out)
+    for r in results[1:]:
+        for it in range(2):
+            for k in range(len(specs)):
+                for a, c in zip(r[it][k], results[0][it][k]):
+                    assert np.array_equal(a, c), (it, k)
+
+
+def test_set_launch_rejects_unknown_shapes(mc):
+    spec = synth.downbranch_model(n_lines=2000, n_packets=100)
+    m = mc.Model(spec, precision=mc.MC_PRECISION_MIXED)
+    m.set_plasma()
+    b = mc.Batch([m])
+    with pytest.raises(mc.MCError):
+        b.set_launch(block=96)
+    with pytest.raises(mc.MCError):
+        b.set_launch(order=9)
+    b.set_launch(block=256, blocks_per_sm=1000)  # clamped to what fits
+    assert 1 <= b.launch()["blocks_per_sm"] <= 8
+    b.close()
+    m.close()

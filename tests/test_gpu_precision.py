@@ -1,0 +1,36 @@
+"""Mixed precision (binary32 distances and optical depths, binary64
+frequencies, resonance tests and estimator sums) against the binary64 oracle,
+measured in units of the Monte Carlo noise.
+
+First iteration of the 500,000-line downbranch model, 1e6 packets, identical
+Sobolev depths on every side.  sigma per shell / spectral bin is the spread of
+8 binary64 GPU runs with independent seeds.  The binary64 GPU run with the
+oracle's seed must agree with the oracle far inside the noise (per-packet
+parity); the mixed run, which shares the oracle's draws, must differ from it
+by less than the noise.  (tests/precision_study.py runs the full study: 10
+iterations with the T_R/W update, a 4e6-packet final iteration, 16 seeds.)
+"""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def report():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import precision_study
+    return precision_study.study(n_loop=1, n_final=0, n_seeds=8)
+
+
+@pytest.mark.parametrize("quantity", ["j_est", "nu_bar", "spectrum"])
+def test_binary64_matches_oracle_inside_the_noise(report, quantity):
+    r = report["iteration0"][quantity]["fp64_gpu_vs_oracle"]
+    assert r["rms"] < 0.05, r
+
+
+@pytest.mark.parametrize("quantity", ["j_est", "nu_bar", "spectrum"])
+def test_mixed_error_below_monte_carlo_noise(report, quantity):
+    r = report["iteration0"][quantity]["mixed_vs_oracle"]
+    assert r["rms"] < 1.0, r
