@@ -371,11 +371,16 @@ def run_batched(args):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     transport_ms = []
+    work = {"segments": 0, "line_checks": 0, "line_interactions": 0, "e_scatters": 0}
     w0 = time.perf_counter()
     ev0.record(stream)
     for it in range(n_it):
         b.run_iteration(seeds, it, n, t_in, update=True)
         transport_ms.append(b.transport_ms())
+        for m in models:  # per-model run statistics (read after the iteration)
+            st = m.spectrum()[1]
+            for k in work:
+                work[k] += st[k]
     b.synchronize()
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -432,6 +437,10 @@ def run_batched(args):
                    "j_blue": bool(specs[0].j_blue), "line_mode": "downbranch",
                    "l2": "inputs larger than L2 (Sobolev depths and J_blue of all models)"},
         "packets_per_s": total_packets * n_it / batched_s,
+        "segments_per_s": work["segments"] / (1e-3 * sum(transport_ms)),
+        "line_checks_per_s": work["line_checks"] / (1e-3 * sum(transport_ms)),
+        "interactions_per_s": (work["line_interactions"] + work["e_scatters"]) / batched_s,
+        "segments_per_packet": work["segments"] / (total_packets * n_it),
         "wall_s": wall_b,
         "transport_ms_per_iteration": transport_ms,
         "autotune": {"launch": tuned, "transport_ms": tuned_ms, "trials": trials, "seconds": tune_s},

@@ -1,5 +1,5 @@
 // Device helpers of the transport kernels: the Philox4x32-10 draw stream,
-// order-preserving integer keys of binary64 values, and the binary64
+// integer comparison keys of binary64 values, and the binary64
 // logarithm and reciprocal used on the hot path.
 #pragma once
 
@@ -62,15 +62,24 @@ struct DrawStream {
   }
 };
 
-// Integer key with the same order as the binary64 value (all finite values;
-// -0 sorts just below +0).  Comparisons of keys run on the integer pipe
-// instead of the binary64 pipe.
-__device__ __forceinline__ long long okey(double v) {
-  const long long b = __double_as_longlong(v);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
-}
+// The bit pattern of a binary64 value read as a signed integer.  Compared
+// with the pattern of a positive value (or +0) it orders exactly like the
+// values do, negative values included (their patterns are negative
+// integers), so every comparison in the transport kernels -- each has one
+// operand known to be positive -- runs on the integer pipe.
+__device__ __forceinline__ long long rawkey(double v) { return __double_as_longlong(v); }
 
-constexpr long long kKeyNegInf = (long long)0x800fffffffffffffll;  // okey(-inf)
+// Pattern of -inf: below every non-negative value's pattern.
+constexpr long long kKeyNegInf = (long long)0xfff0000000000000ll;
+
+// A pattern below that of every non-negative value.
+constexpr long long kRawBelowZero = (long long)0x8000000000000000ll;
+
+// v < 0, excluding -0 (its pattern is the most negative integer).
+__device__ __forceinline__ bool strictly_negative(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 && b != kRawBelowZero;
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;

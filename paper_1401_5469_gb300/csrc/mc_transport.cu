@@ -18,7 +18,8 @@
 //    line of depth tau moves nu_e up by tau nu_lab / k (one FMA), and the line
 //    absorbs the packet exactly when that new nu_e exceeds nu_line (Sect. 2.6's
 //    test tau_S + kappa d_line > tau with kappa d = (nu_cmf - nu) / (nu_lab/k));
-//    every comparison is an integer compare of order-preserving keys;
+//    every comparison is an integer compare of the values' bit patterns
+//    (one operand is always positive, so the patterns order like the values);
 //  * 1/D and 1/nu_lab are carried and refreshed with Newton reciprocals, and
 //    -ln z comes from a table-driven logarithm;
 //  * downbranch emission is an integer guide-table search, and the next
@@ -110,7 +111,7 @@ __device__ __forceinline__ Emission downbranch_pick(const TransportParams &p, in
 }
 
 // max(v, 0) through the integer keys (no binary64 instruction).
-__device__ __forceinline__ double max0(double v) { return okey(v) > 0 ? v : 0.0; }
+__device__ __forceinline__ double max0(double v) { return rawkey(v) > 0 ? v : 0.0; }
 
 // x mu at the shell exit: +sqrt(x_out^2 - q), or -sqrt(x_in^2 - q) when the
 // ray meets the inner sphere.
@@ -127,8 +128,8 @@ __device__ __forceinline__ double shell_exit(double q, bool inner, double xi2, d
 __device__ __forceinline__ bool inside_shell(double pp, double q, double l, bool inner, double xi2,
                                              double xo2) {
   const double pl = pp + l;
-  const long long k2 = okey(fma(pl, pl, q));
-  return inner ? (okey(pl) < -1 && k2 > okey(xi2)) : k2 < okey(xo2);
+  const long long k2 = rawkey(fma(pl, pl, q));  // all three squares are >= 0
+  return inner ? (strictly_negative(pl) && k2 > rawkey(xi2)) : k2 < rawkey(xo2);
 }
 
 // Injection at the inner boundary, Sect. 2.4: Planck-sampled comoving
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       // inner sphere is hit when moving inward with q <= x_in^2), so the path
       // length is p_exit - p and the comoving frequency there nu_lab (1 - p_exit).
       const double xi2 = s_xi2[s], xo2 = s_xo2[s];
-      const bool inner = okey(pp) < -1 && okey(q) <= okey(xi2);  // p < 0 (not -0)
+      const bool inner = strictly_negative(pp) && rawkey(q) <= rawkey(xi2);  // q, x_in^2 >= 0
       // The root (one binary64 square root, ~650 cycles) is taken only when
       // a line is passed or the shell event wins: an event at path length l
       // lies inside the shell exactly when the radius there, x^2 = q + (p+l)^2,
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       if (thomson) {
         c_e = (nu_lab * s_ikap[s]) * inv_D;  // nu_lab / k, k = kappa' D
         thr_e = fma(-tau_rem, c_e, nu_cmf);
-        key_e = okey(thr_e);
+        key_e = rawkey(thr_e);
       }
       long long key_thr = key_e;  // the shell threshold joins once known
       const double e_inv2 = JB ? (pk.e_lab * inv_nu) * inv_nu : 0.0;
@@ -302,9 +303,9 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         double t = 0.0;
         if (thomson) {
           t = fma(taul, c_e, thr_e);
-          absorbed = okey(t) > bj;
+          absorbed = rawkey(t) > bj;  // nu_j > 0
         } else {
-          absorbed = okey(taul) > okey(tau_rem);
+          absorbed = rawkey(taul) > rawkey(tau_rem);  // both >= 0
         }
         if (absorbed) {
           const double lj = max0(fma(-nuj, inv_nu, D));
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         }
         if (!have_shell) {  // a line is passed: the scan needs the exit threshold
           p_exit = shell_exit(q, inner, xi2, xo2);
-          key_shell = okey(nu_lab * (1.0 - p_exit));
+          key_shell = rawkey(nu_lab * (1.0 - p_exit));  // > 0
           have_shell = true;
           key_thr = key_shell > key_e ? key_shell : key_e;
           if (bj <= key_shell) break;  // this line lies beyond the exit
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         if (JB) atomicAdd(p.j_blue + row + j, nuj * e_inv2);
         if (thomson) {
           thr_e = t;
-          key_e = okey(t);
+          key_e = rawkey(t);
           key_thr = key_shell > key_e ? key_shell : key_e;
         } else {
           tau_rem -= taul;

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
       if (thomson) {
         c_e = (static_cast<float>(nu_lab) * c.ikap[s]) * inv_D;  // nu_lab / k
         thr_e = nu_cmf - static_cast<double>(tau0 * c_e);
-        key_e = okey(thr_e);
+        key_e = rawkey(thr_e);  // compared only with positive keys
       }
       long long key_thr = key_e;
       const float e_inv2 = JB ? (pk.e_lab * inv_nu) * inv_nu : 0.0f;
@@ -350,14 +350,14 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
         double t = 0.0;
         if (thomson) {
           t = thr_e + static_cast<double>(taul * c_e);
-          absorbed = okey(t) > bj;
+          absorbed = rawkey(t) > bj;  // nu_j > 0
         } else {
           absorbed = taul > tau_rem;
         }
         if (!absorbed) {
           if (!have_shell) {  // a line is passed: the scan needs the exit threshold
             p_exit = shell_exit_f(q, inner, xi2, xo2);
-            key_shell = okey(nu_lab * static_cast<double>(1.0f - p_exit));
+            key_shell = rawkey(nu_lab * static_cast<double>(1.0f - p_exit));  // > 0
             have_shell = true;
             key_thr = key_shell > key_e ? key_shell : key_e;
             if (bj <= key_shell) break;  // this line lies beyond the exit
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
           if (JB) atomicAdd(c.j_blue + row + j, static_cast<double>(static_cast<float>(nuj) * e_inv2) * c.e_cmf);
           if (thomson) {
             thr_e = t;
-            key_e = okey(t);
+            key_e = rawkey(t);
             key_thr = key_shell > key_e ? key_shell : key_e;
           } else {
             tau_rem -= taul;
