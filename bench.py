@@ -167,7 +167,8 @@ def run_reference(args):
 
 
 def cpu_baseline_sample(spec, seconds_hint=10.0):
-    """Oracle throughput on a bounded sample of the workload (first iteration)."""
+    """Oracle throughput on a bounded sample of the workload (first iteration),
+    on all host cores and on one, with the counted work of the sample."""
     import oracle
     threads = os.cpu_count() or 1
     t_rad = np.full(spec.n_shells, 1.0e4)
@@ -175,11 +176,49 @@ def cpu_baseline_sample(spec, seconds_hint=10.0):
     om = oracle.OracleModel(spec, tau=oracle.plasma_tau(spec, t_rad, w))
     n = int(os.environ.get("BENCH_CPU_SAMPLE", "100000"))
     t0 = time.perf_counter()
-    oracle.run_iteration(om, spec.seed, 0, spec.n_packets, spec.t_inner, first=0, count=n,
-                         threads=threads, record=False)
+    r = oracle.run_iteration(om, spec.seed, 0, spec.n_packets, spec.t_inner, first=0, count=n,
+                             threads=threads, record=False)
     dt = time.perf_counter() - t0
+    n1 = max(1, n // 16)
+    t0 = time.perf_counter()
+    oracle.run_iteration(om, spec.seed, 0, spec.n_packets, spec.t_inner, first=0, count=n1,
+                         threads=1, record=False)
+    dt1 = time.perf_counter() - t0
+    st = r.stats
     return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {n} of the 1e6 packets of iteration 0 ({dt:.1f} s)"}
+            "sample": f"first {n} of the 1e6 packets of iteration 0 ({dt:.1f} s)",
+            "interactions_per_s": (st["line_interactions"] + st["e_scatters"]) / dt,
+            "line_checks_per_s": st["line_checks"] / dt,
+            "single_thread": {"value": n1 / dt1, "unit": UNIT,
+                              "sample": f"first {n1} packets of iteration 0 ({dt1:.1f} s)"}}
+
+
+def scatter_config(mc, synth):
+    """The 2000-line scatter model (20 shells, 1e4 packets, tau given), one
+    iteration: GPU transport time (CUDA events) and the oracle on all host
+    cores, both over the whole iteration."""
+    spec = synth.scatter_model()
+    m = mc.Model(spec)
+    m.set_plasma(tau=spec.tau)
+    for it in range(3):  # warm-up
+        m.run_iteration(spec.seed, it, spec.n_packets, spec.t_inner)
+    ms = []
+    for it in range(3, 8):
+        m.run_iteration(spec.seed, it, spec.n_packets, spec.t_inner)
+        ms.append(float(m.timing()[1]))
+    m.close()
+    out = {"workload": "scatter-20sh-2000-lines-1e4-packets", "gpu_transport_ms": float(np.median(ms)),
+           "gpu_packets_per_s": spec.n_packets / (1e-3 * float(np.median(ms)))}
+    if os.environ.get("BENCH_SKIP_CPU") != "1":
+        import oracle
+        om = oracle.OracleModel(spec, tau=spec.tau)
+        t0 = time.perf_counter()
+        oracle.run_iteration(om, spec.seed, 0, spec.n_packets, spec.t_inner, threads=os.cpu_count() or 1,
+                             record=False)
+        dt = time.perf_counter() - t0
+        out["cpu_oracle_packets_per_s"] = spec.n_packets / dt
+        out["cpu_cores"] = os.cpu_count() or 1
+    return out
 
 
 def run_ours(args):
@@ -261,6 +300,7 @@ def run_ours(args):
 
     m.close()
     mixed = measure_mixed(spec, seed, args) if os.environ.get("BENCH_SKIP_MIXED") != "1" else None
+    scatter = scatter_config(mc, synth) if rank == 0 else None
     if rank != 0:
         return 0
     ms_step = 1e3 * elapsed / args.steps
@@ -295,6 +335,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "mixed_precision": mixed,
+        "scatter_config": scatter,
     }
     print(json.dumps(line), flush=True)
     return 0

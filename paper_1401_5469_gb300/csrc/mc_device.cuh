@@ -42,6 +42,9 @@ struct DrawStream {
       wa = spare_a; wb = spare_b;
     }
     ++d;
+    return u53_of(wa, wb);
+  }
+  static __device__ __forceinline__ uint64_t u53_of(uint32_t wa, uint32_t wb) {
     return (static_cast<uint64_t>(wa >> 5) << 26) | static_cast<uint64_t>(wb >> 6);
   }
   // z in (0, 1]
@@ -50,8 +53,9 @@ struct DrawStream {
   __device__ __forceinline__ double closed0() { return __ull2double_rn(next_u53()) * 0x1.0p-53; }
   // mu = 2 z - 1 for z = u53 2^-53 in [0, 1): (u53 - 2^52) 2^-52, exact.
   // Assembled from the integer's bits (no conversion instruction).
-  __device__ __forceinline__ double mu_isotropic() {
-    const long long v = static_cast<long long>(next_u53()) - (1ll << 52);
+  __device__ __forceinline__ double mu_isotropic() { return mu_from_u53(next_u53()); }
+  static __device__ __forceinline__ double mu_from_u53(unsigned long long u) {
+    const long long v = static_cast<long long>(u) - (1ll << 52);
     const unsigned long long a = static_cast<unsigned long long>(v < 0 ? -v : v);  // <= 2^52
     if (a == 0ull) return 0.0;
     const int lz = __clzll(static_cast<long long>(a));
@@ -164,6 +168,66 @@ __device__ __forceinline__ double neg_log_u53(unsigned long long u) {
   p = fma(p, r, 1.0);
   return -((kl.x + ct.y) + fma(p, r, kl.y));
 }
+
+// Draws of a warp's last live packet, computed ahead by the whole warp.
+// Once the packet queue is empty and one lane of a warp is left, the other
+// 31 lanes have nothing to do; a draw's value depends only on (key, packet,
+// iteration, draw index), so lane i computes Philox block base/2 + i and the
+// -ln z of both its draws, and the live lane reads its next 64 draws from
+// shared memory instead of running Philox and the log on its own dependency
+// chain.  Values are identical to DrawStream's.  All state is warp-uniform.
+// (Serving up to four live lanes, with per-lane slots, measured slower: the
+// per-segment bookkeeping then costs more than the draws it saves.)
+constexpr uint32_t kWarpDraws = 64;
+constexpr uint32_t kNoPacket = 0xffffffffu;
+
+struct WarpDraws {
+  unsigned long long *u;  // [64] u53 of draws base .. base + 63 (shared memory, per warp)
+  double *t;              // [64] -ln((u53 + 1) 2^-53) of the same draws
+  uint32_t base, pid;     // first draw index held, packet (kNoPacket: none)
+  bool on;                // the warp is down to one live lane, which reads the buffer
+
+  __device__ __forceinline__ void init(unsigned long long *warp_buf) {
+    u = warp_buf;
+    t = reinterpret_cast<double *>(warp_buf + kWarpDraws);
+    base = 0u;
+    pid = kNoPacket;
+    on = false;
+  }
+
+  // All 32 lanes, converged, after the claim step.  alive: this lane has a
+  // packet; drained: the packet queue is empty.  With one live lane left,
+  // refill the buffer when it holds fewer than the three draws a segment may
+  // take (or belongs to another packet).
+  __device__ __forceinline__ void prepare(bool alive, bool drained, const DrawStream &ds,
+                                          uint32_t packet, uint32_t k0, uint32_t k1,
+                                          uint32_t iteration, unsigned lane) {
+    const unsigned live = __ballot_sync(0xffffffffu, alive);
+    on = drained && __popc(live) == 1;
+    if (!on) return;
+    const int owner = __ffs(live) - 1;
+    const uint32_t d = __shfl_sync(0xffffffffu, ds.d, owner);
+    const uint32_t pk = __shfl_sync(0xffffffffu, packet, owner);
+    if (pk == pid && d + 3u <= base + kWarpDraws) return;
+    const uint32_t b = d & ~1u;
+    const uint4 o = philox4x32_10(make_uint4((b >> 1) + lane, pk, iteration, 0u), k0, k1);
+    const unsigned long long u0 = DrawStream::u53_of(o.x, o.y), u1 = DrawStream::u53_of(o.z, o.w);
+    u[2 * lane] = u0;
+    u[2 * lane + 1] = u1;
+    t[2 * lane] = neg_log_u53(u0 + 1ull);
+    t[2 * lane + 1] = neg_log_u53(u1 + 1ull);
+    __syncwarp();
+    base = b;
+    pid = pk;
+  }
+  // The live lane's next draw (u53, or the -ln z of an open-interval draw).
+  __device__ __forceinline__ unsigned long long next_u53(DrawStream &ds) const {
+    return on ? u[ds.d++ - base] : ds.next_u53();
+  }
+  __device__ __forceinline__ double next_tau(DrawStream &ds) const {
+    return on ? t[ds.d++ - base] : neg_log_u53(ds.next_u53() + 1ull);
+  }
+};
 
 // ln(x) for a positive normal binary64 x.
 __device__ __forceinline__ double log_pos(double x) {

@@ -186,6 +186,9 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
 
   Packet pk;
   DrawStream ds;
+  WarpDraws wd;
+  wd.init(reinterpret_cast<unsigned long long *>(sh + kShellArrays * S) +
+          2 * kWarpDraws * (threadIdx.x >> 5));
   bool alive = false, finished = false;
   unsigned long long n_esc = 0, n_reab = 0, n_cap = 0, n_seg = 0, n_chk = 0, n_res = 0, n_lint = 0,
                      n_esca = 0, n_shell = 0;
@@ -226,6 +229,8 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         break;
       }
     }
+    // ---- a warp's last live walk: the idle lanes compute its draws ahead
+    wd.prepare(alive, __any_sync(0xffffffffu, finished), ds, pk.pid, p.key0, p.key1, p.iteration, lane);
     if (!alive) continue;
 
     // ---- one flight segment (Sect. 2.6)
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       const double kap = s_kap[s];
       const bool thomson = kap > 0.0;
       // optical depth to the next event, tau = -ln z
-      double tau_rem = neg_log_u53(ds.next_u53() + 1ull);
+      double tau_rem = wd.next_tau(ds);
       // Shell boundary: at the exit point x mu = p_exit = +-sqrt(x_b^2 - q) (the
       // inner sphere is hit when moving inward with q <= x_in^2), so the path
       // length is p_exit - p and the comoving frequency there nu_lab (1 - p_exit).
@@ -383,7 +388,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         if (kind == kLineEvent) {
           pk.cnt[3] += 1u;
           if (MODE == 1) {
-            const Emission em = downbranch_pick(p, j, rinfo_hit, ds.next_u53());
+            const Emission em = downbranch_pick(p, j, rinfo_hit, wd.next_u53(ds));
             nu_c = em.nu;
             inv_nu_c = em.inv_nu;
             pk.next_line = em.line + 1;
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
           inv_nu_c = inv_nu * rcp64(D1);
         }
         // isotropic re-emission: new direction, lab values from the comoving ones
-        const double mu2 = ds.mu_isotropic();
+        const double mu2 = DrawStream::mu_from_u53(wd.next_u53(ds));
         const double pn = xn * mu2;
         const double D2 = 1.0 - pn;
         const double iD2 = rcp64(D2);
@@ -474,7 +479,10 @@ const void *select_kernel(int line_mode, int precision, bool jb, bool rec) {
 }
 
 size_t smem_bytes(int S, int precision) {
-  return precision == 1 ? mixed_smem_bytes(S) : static_cast<size_t>(kShellArrays) * S * sizeof(double);
+  // binary64: shell tables, then one WarpDraws buffer (u53 + -ln z) per warp
+  return precision == 1 ? mixed_smem_bytes(S)
+                        : static_cast<size_t>(kShellArrays) * S * sizeof(double) +
+                              (kBlock / 32) * 2 * kWarpDraws * sizeof(double);
 }
 
 }  // namespace
@@ -490,6 +498,8 @@ cudaError_t transport_occupancy(int line_mode, int precision, bool j_blue, bool 
 
 cudaError_t launch_transport(const TransportParams &p, int line_mode, int precision, bool j_blue,
                              bool record, int grid, int block, cudaStream_t st) {
+  // the shared-memory layout (one draw buffer per warp) is sized for kBlock
+  if (block != kBlock) return cudaErrorInvalidValue;
   const void *k = select_kernel(line_mode, precision, j_blue, record);
   const size_t smem = smem_bytes(p.S, precision);
   if (smem > 48 * 1024) {
