@@ -52,6 +52,27 @@ UNIT = "packets/s"
 WORKLOAD = "downbranch-20sh-500k-lines-1e6-packets"
 L2_BYTES = 129 * 2**20
 
+# DRAM traffic of one transport_fp64 launch of this workload (1e6 packets,
+# iteration 0), from the one-pass ncu capture summarised in
+# profiles/transport_fp64_downbranch_500k_traffic.md.  It stands for the
+# kernel built from these sources only: with any other source hash the
+# bench reports traffic as null.
+TRAFFIC_CAPTURE = {
+    "dram_bytes_per_launch": 623.64e6 + 111.88e6,
+    "sources": ("paper_1401_5469_gb300/csrc/mc_transport.cu", "paper_1401_5469_gb300/csrc/mc_device.cuh",
+                "paper_1401_5469_gb300/csrc/mc_internal.h"),
+    "sha256": "c495aef9f0a8dd4eef95cf2190aef0fdc1dff1d8058105c998ac245a2112aa5e",
+}
+
+
+def _captured_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TRAFFIC_CAPTURE["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return TRAFFIC_CAPTURE["dram_bytes_per_launch"] if h.hexdigest() == TRAFFIC_CAPTURE["sha256"] else None
+
 
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -328,8 +349,8 @@ def run_ours(args):
         "transport_phases_ms": {"queue_drain": phase_ms[0] / args.steps, "tail": phase_ms[1] / args.steps},
         "per_step": per,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "transport_fp64",
-                     "peak_kind": peak_kind},
+                     "frac": achieved / peak, "traffic": _captured_traffic(), "kernel": "transport_fp64",
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes},
         "cpu_baseline": cpu,
         "e2e": {"value": ws * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
