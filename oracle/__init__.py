@@ -75,6 +75,8 @@ class _Model(C.Structure):
         ("spec_nu_lo", C.c_double), ("spec_nu_hi", C.c_double),
         ("max_segments", C.c_uint64),
         ("delta_t", C.c_double),
+        ("n_virtual", C.c_int32),
+        ("tau_v_max", C.c_double),
     ]
 
 
@@ -85,6 +87,7 @@ class _Result(C.Structure):
         ("stats", C.c_uint64 * NSTATS),
         ("status", C.c_void_p), ("nu_out", C.c_void_p), ("e_out", C.c_void_p),
         ("counters", C.c_void_p),
+        ("spectrum_v", C.c_void_p),
     ]
 
 
@@ -123,6 +126,8 @@ def lib():
             L.orc_run_traced.restype = i32
             L.orc_run_traced.argtypes = [C.POINTER(_Model), u64, u32, u64, d, u64, u64,
                                          C.POINTER(_Result), C.POINTER(_Trace)]
+            L.orc_virtual_tau.restype = d
+            L.orc_virtual_tau.argtypes = [C.POINTER(_Model), d, d, i32, d, i32]
             L.orc_inject_packets.restype = i32
             L.orc_inject_packets.argtypes = [C.POINTER(_Model), u64, u32, u64, d, u64, u64, vp, vp, vp, vp, vp]
             L.orc_uniforms.argtypes = [u64, u32, u32, u32, i64, vp]
@@ -221,6 +226,15 @@ class OracleModel:
             self.dbr_offset = self.dbr_line = self.dbr_cdf = None
         self.max_segments = int(max_segments)
         self.delta_t = float(delta_t)
+        self.n_virtual = 0
+        self.tau_v_max = 0.0
+        self._refresh()
+
+    def set_virtual(self, n_virtual: int, tau_v_max: float = 0.0):
+        """Virtual packets (Sect. 2.9) in subsequent runs: N_v per launch;
+        a v-packet whose optical depth exceeds tau_v_max (> 0) is dropped."""
+        self.n_virtual = int(n_virtual)
+        self.tau_v_max = float(tau_v_max)
         self._refresh()
 
     def set_tau(self, tau):
@@ -235,7 +249,8 @@ class OracleModel:
             tau=_p(self.tau), line_mode=self.line_mode, line_row=_p(self.line_row),
             dbr_offset=_p(self.dbr_offset), dbr_line=_p(self.dbr_line), dbr_cdf=_p(self.dbr_cdf),
             j_blue=self.j_blue, spec_bins=int(s.spec_bins), spec_nu_lo=float(s.spec_nu_lo),
-            spec_nu_hi=float(s.spec_nu_hi), max_segments=self.max_segments, delta_t=self.delta_t)
+            spec_nu_hi=float(s.spec_nu_hi), max_segments=self.max_segments, delta_t=self.delta_t,
+            n_virtual=self.n_virtual, tau_v_max=self.tau_v_max)
 
 
 class OracleResult:
@@ -255,6 +270,7 @@ def run_iteration(om: OracleModel, seed: int, iteration: int, n_packets: int, t_
     want_jb = om.j_blue if j_blue is None else j_blue
     r.j_blue = np.zeros((S, L)) if want_jb else None
     r.spectrum = np.zeros(B + 2)
+    r.spectrum_v = np.zeros(B + 2) if om.n_virtual > 0 else None
     if record:
         r.status = np.zeros(count, dtype=np.int32)
         r.nu = np.zeros(count)
@@ -264,7 +280,7 @@ def run_iteration(om: OracleModel, seed: int, iteration: int, n_packets: int, t_
         r.status = r.nu = r.energy = r.counters = None
     res = _Result(j_est=_p(r.j_est), nu_bar=_p(r.nu_bar), j_blue=_p(r.j_blue),
                   spectrum=_p(r.spectrum), status=_p(r.status), nu_out=_p(r.nu),
-                  e_out=_p(r.energy), counters=_p(r.counters))
+                  e_out=_p(r.energy), counters=_p(r.counters), spectrum_v=_p(r.spectrum_v))
     rc = lib().orc_run(C.byref(om.c), seed, iteration, n_packets, float(t_inner), first, count,
                        threads, C.byref(res))
     if rc != 0:
@@ -283,7 +299,7 @@ def run_traced(om: OracleModel, seed, iteration, n_packets, t_inner, first, coun
     r.counters = np.zeros((count, NCOUNT), dtype=np.uint64)
     res = _Result(j_est=_p(r.j_est), nu_bar=_p(r.nu_bar), j_blue=_p(r.j_blue),
                   spectrum=_p(r.spectrum), status=_p(r.status), nu_out=_p(r.nu),
-                  e_out=_p(r.energy), counters=_p(r.counters))
+                  e_out=_p(r.energy), counters=_p(r.counters), spectrum_v=_p(r.spectrum_v))
     ev = (_Event * capacity)()
     tr = _Trace(events=C.cast(ev, C.c_void_p), capacity=capacity, count=0)
     rc = lib().orc_run_traced(C.byref(om.c), seed, iteration, n_packets, float(t_inner), first,
@@ -310,6 +326,15 @@ def inject_packets(om: OracleModel, seed, iteration, n_packets, t_inner, first=0
         raise ValueError("oracle rejected the model")
     out["next_line"] = nl
     return out
+
+
+def virtual_tau(om: OracleModel, x: float, mu: float, shell: int, nu_lab: float, next_line: int) -> float:
+    """Optical depth tau_v of a virtual packet from radius x (units of c t_exp)
+    in direction mu, shell `shell`, lab frequency nu_lab, lines from next_line
+    on, to the outer boundary (Sect. 2.9); inf if it meets the inner boundary
+    or exceeds the model's tau_v_max."""
+    return float(lib().orc_virtual_tau(C.byref(om.c), float(x), float(mu), int(shell), float(nu_lab),
+                                       int(next_line)))
 
 
 def downbranch_pick(om: OracleModel, row: int, z: float) -> int:

@@ -284,6 +284,8 @@ typedef struct {
     double spec_nu_lo, spec_nu_hi;
     uint64_t max_segments;
     double delta_t;                        /* s */
+    int32_t n_virtual;                     /* N_v virtual packets per launch (Sect. 2.9), 0 = off */
+    double tau_v_max;                      /* drop a v-packet once tau_v exceeds this (0 = never) */
 } orc_model;
 
 typedef struct {
@@ -297,6 +299,7 @@ typedef struct {
     double *nu_out;     /* lab frequency at the end */
     double *e_out;      /* lab energy at the end */
     uint64_t *counters; /* [count * ORC_NCOUNT] */
+    double *spectrum_v; /* [bins+2] sum E_v,lab exp(-tau_v) per bin (Eq. 21), or NULL */
 } orc_result;
 
 /* Per-event trace for the invariant tests (small runs only). */
@@ -422,6 +425,92 @@ static void inject(const orc_model *m, const orc_geom *g, orc_rng *r, double e_c
     if (nu_cmf_out) *nu_cmf_out = nu_cmf;
 }
 
+static void spectrum_add(const orc_model *m, double *spec, double nu_lab, double e_lab);
+
+/* ------------------------------------------------------------ virtual packets
+ * Sect. 2.9.  In the spectrum iteration, whenever an r-packet is about to
+ * start a new trajectory (injection, or after an interaction), N_v virtual
+ * packets leave the same point with the same comoving frequency and energy
+ * but their own directions mu_v, uniform in (mu_min, 1] with
+ * mu_min = -sqrt(1 - (r_inner/r)^2), so that none meets the inner boundary.
+ * A v-packet never interacts: it flies to the outer boundary collecting the
+ * optical depth tau_v of the Sobolev points it passes and of electron
+ * scattering (kappa_e = sigma_T n_e D with D at each segment start, as for
+ * r-packets), and adds exp(-tau_v) times its lab-frame energy to the bin of
+ * its lab frequency (Eq. 21).  Comoving energies: Eq. 19 after an
+ * interaction, Eq. 20 at injection.  Its direction draws come from Philox
+ * stream 1, so the r-packet's own draws are untouched.
+ */
+
+/* tau_v along the ray from x, mu in shell s (lines from index j on), or
+ * ORC_INF when the ray meets the inner boundary (only by rounding) or tau_v
+ * exceeds tau_v_max (> 0). */
+static double virtual_tau(const orc_model *m, const orc_geom *g, double x, double mu, int32_t s,
+                          double nu_lab, int32_t j)
+{
+    const int32_t S = m->n_shells, L = m->n_lines;
+    const double inv = 1.0 / nu_lab;
+    double tau = 0.0;
+    for (;;) {
+        const double D = 1.0 - mu * x;
+        const double nu_cmf = nu_lab * D;
+        const double kv = g->kappa[s] * D;
+        int32_t which;
+        const double d_shell = orc_distance_shell(x, mu, g->x_in[s], g->x_out[s], &which);
+        /* Sobolev points before the shell boundary (strict, as for r-packets) */
+        while (j < L) {
+            double d_line = (nu_cmf - m->nu[j]) * inv;
+            if (d_line < 0.0) d_line = 0.0;
+            if (!(d_line < d_shell)) break;
+            tau += m->tau[(size_t)s * (size_t)L + (size_t)j];
+            j += 1;
+            if (m->tau_v_max > 0.0 && tau > m->tau_v_max) return ORC_INF;
+        }
+        tau += kv * d_shell;
+        if (m->tau_v_max > 0.0 && tau > m->tau_v_max) return ORC_INF;
+        const double xb = (which > 0) ? g->x_out[s] : g->x_in[s];
+        double mun = (x * mu + d_shell) / xb;
+        if (mun > 1.0) mun = 1.0;
+        if (mun < -1.0) mun = -1.0;
+        x = xb;
+        mu = mun;
+        s += which;
+        if (s >= S) return tau;
+        if (s < 0) return ORC_INF;
+    }
+}
+
+double orc_virtual_tau(const orc_model *m, double x, double mu, int32_t shell, double nu_lab, int32_t next_line)
+{
+    orc_geom g;
+    geom_init(m, &g);
+    double tau = virtual_tau(m, &g, x, mu, shell, nu_lab, next_line);
+    geom_free(&g);
+    return tau;
+}
+
+/* N_v v-packets from radius x in shell s with comoving frequency nu_cmf and
+ * comoving energy e_cmf of the r-packet about to be launched. */
+static void spawn_virtual(const orc_model *m, const orc_geom *g, orc_rng *rv, double x, int32_t s,
+                          double nu_cmf, double e_cmf, int32_t next_line, int injection, orc_result *res)
+{
+    const int32_t nv = m->n_virtual;
+    const double ri = g->x_in[0] / x;
+    double arg = 1.0 - ri * ri;
+    if (arg < 0.0) arg = 0.0;
+    const double mu_min = -sqrt(arg);
+    for (int32_t i = 0; i < nv; ++i) {
+        const double mu_v = mu_min + (1.0 - mu_min) * rng_open0(rv);
+        const double D = 1.0 - mu_v * x;
+        const double e_v = injection ? (e_cmf * (2.0 * mu_v)) / (double)nv
+                                     : (e_cmf * (1.0 - mu_min)) / (2.0 * (double)nv);
+        const double nu_lab = nu_cmf / D;
+        const double tau = virtual_tau(m, g, x, mu_v, s, nu_lab, next_line);
+        if (tau == ORC_INF) continue;
+        spectrum_add(m, res->spectrum_v, nu_lab, (e_v / D) * orc_exp(-tau));
+    }
+}
+
 static void trace_push(orc_trace *t, const orc_event *e)
 {
     if (t && t->count < t->capacity) t->events[t->count] = *e;
@@ -430,7 +519,7 @@ static void trace_push(orc_trace *t, const orc_event *e)
 
 /* Transport one packet until it escapes, is reabsorbed or is capped
  * (Sect. 2.6), accumulating the estimators of Sect. 2.7 into res. */
-static void transport(const orc_model *m, const orc_geom *g, orc_rng *r, orc_packet *pk,
+static void transport(const orc_model *m, const orc_geom *g, orc_rng *r, orc_rng *rv, orc_packet *pk,
                       orc_result *res, orc_trace *trace)
 {
     const int32_t S = m->n_shells, L = m->n_lines;
@@ -539,6 +628,7 @@ static void transport(const orc_model *m, const orc_geom *g, orc_rng *r, orc_pac
             pk->mu = mu2;
             pk->nu_lab = nu_c / D2;
             pk->e_lab = e_c / D2;
+            if (rv) spawn_virtual(m, g, rv, xn, s, nu_c, e_c, j, 0, res);
             if (trace) {
                 ev.kind = 1; ev.x = xn; ev.mu_after = mu2;
                 ev.nu_cmf_before = nu_c; ev.nu_cmf_after = pk->nu_lab * D2;
@@ -564,6 +654,7 @@ static void transport(const orc_model *m, const orc_geom *g, orc_rng *r, orc_pac
             pk->nu_lab = nu_line[emit] / D2;
             pk->e_lab = e_c / D2;
             pk->next_line = emit + 1;
+            if (rv) spawn_virtual(m, g, rv, xn, s, nu_line[emit], e_c, emit + 1, 0, res);
             if (trace) {
                 ev.nu_cmf_after = pk->nu_lab * D2; ev.e_cmf_after = pk->e_lab * D2;
                 ev.nu_lab_after = pk->nu_lab; ev.e_lab_after = pk->e_lab;
@@ -595,8 +686,15 @@ static void run_range(const orc_model *m, const orc_geom *g, uint64_t seed, uint
         orc_rng r;
         rng_init(&r, seed, iteration, (uint32_t)pid, 0u);
         orc_packet pk;
-        inject(m, g, &r, e_cmf, t_inner, &pk, NULL);
-        transport(m, g, &r, &pk, res, trace);
+        double nu_cmf0;
+        inject(m, g, &r, e_cmf, t_inner, &pk, &nu_cmf0);
+        orc_rng rv;
+        const int virt = m->n_virtual > 0 && res->spectrum_v;
+        if (virt) {
+            rng_init(&rv, seed, iteration, (uint32_t)pid, 1u);
+            spawn_virtual(m, g, &rv, g->x_in[0], 0, nu_cmf0, e_cmf, pk.next_line, 1, res);
+        }
+        transport(m, g, &r, virt ? &rv : NULL, &pk, res, trace);
         if (pk.status == ORC_ESCAPED) {
             res->stats[ORC_ST_ESCAPED] += 1;
             spectrum_add(m, res->spectrum, pk.nu_lab, pk.e_lab);
@@ -675,6 +773,7 @@ int orc_run(const orc_model *m, uint64_t seed, uint32_t iteration, uint64_t n_pa
         jb->res.nu_bar = (double *)calloc((size_t)S, sizeof(double));
         jb->res.spectrum = (double *)calloc((size_t)B + 2, sizeof(double));
         jb->res.j_blue = nJb ? (double *)calloc(nJb, sizeof(double)) : NULL;
+        jb->res.spectrum_v = res->spectrum_v ? (double *)calloc((size_t)B + 2, sizeof(double)) : NULL;
         jb->res.status = res->status ? res->status + off : NULL;
         jb->res.nu_out = res->nu_out ? res->nu_out + off : NULL;
         jb->res.e_out = res->e_out ? res->e_out + off : NULL;
@@ -687,9 +786,12 @@ int orc_run(const orc_model *m, uint64_t seed, uint32_t iteration, uint64_t n_pa
         orc_job *jb = &jobs[t];
         for (int s = 0; s < S; ++s) { res->j_est[s] += jb->res.j_est[s]; res->nu_bar[s] += jb->res.nu_bar[s]; }
         for (int b = 0; b < B + 2; ++b) res->spectrum[b] += jb->res.spectrum[b];
+        if (res->spectrum_v)
+            for (int b = 0; b < B + 2; ++b) res->spectrum_v[b] += jb->res.spectrum_v[b];
         for (size_t i = 0; i < nJb; ++i) res->j_blue[i] += jb->res.j_blue[i];
         for (int k = 0; k < ORC_NSTATS; ++k) res->stats[k] += jb->res.stats[k];
         free(jb->res.j_est); free(jb->res.nu_bar); free(jb->res.spectrum); free(jb->res.j_blue);
+        free(jb->res.spectrum_v);
     }
     free(jobs); free(th);
     geom_free(&g);

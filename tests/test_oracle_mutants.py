@@ -50,6 +50,24 @@ MUTANTS = [
     ("geometric dilution from the inverse ratio", "double rr = x_i / x_mid;",
      "double rr = x_mid / x_i;", 1,
      "tests/test_oracle_plasma.py::test_geometric_dilution_is_solid_angle_fraction"),
+    ("Eq. 19 weight with 1 + mu_min", "(e_cmf * (1.0 - mu_min)) / (2.0 * (double)nv)",
+     "(e_cmf * (1.0 + mu_min)) / (2.0 * (double)nv)", 1,
+     "tests/test_oracle_virtual.py::test_scattering_model_v_and_r_spectra_agree_and_v_is_less_noisy"),
+    ("v-packet energy left in the comoving frame", "(e_v / D) * orc_exp(-tau)", "e_v * orc_exp(-tau)", 1,
+     "tests/test_oracle_virtual.py::test_free_streaming_total_matches_closed_form"),
+    ("v-packet depth without electron scattering", "        tau += kv * d_shell;",
+     "        tau += 0.0 * d_shell;", 1,
+     "tests/test_oracle_virtual.py::test_radial_electron_optical_depth"),
+    ("v-packet line depth from the neighbouring shell",
+     "tau += m->tau[(size_t)s * (size_t)L + (size_t)j];",
+     "tau += m->tau[(size_t)(s > 0 ? s - 1 : s + 1) * (size_t)L + (size_t)j];", 1,
+     "tests/test_oracle_virtual.py::test_single_line_depth_counts_only_in_its_shell"),
+    ("v-packets drawing from the r-packet stream", "transport(m, g, &r, virt ? &rv : NULL,",
+     "transport(m, g, &r, virt ? &r : NULL,", 1,
+     "tests/test_oracle_virtual.py::test_r_packets_unchanged_by_virtual_packets"),
+    ("v-packet directions only outward", "const double mu_min = -sqrt(arg);",
+     "const double mu_min = sqrt(arg);", 1,
+     "tests/test_oracle_virtual.py::test_scattering_model_v_and_r_spectra_agree_and_v_is_less_noisy"),
 ]
 
 
