@@ -294,6 +294,7 @@ def run_traced(om: OracleModel, seed, iteration, n_packets, t_inner, first, coun
     r = OracleResult()
     r.j_est, r.nu_bar, r.spectrum = np.zeros(S), np.zeros(S), np.zeros(B + 2)
     r.j_blue = np.zeros((S, L)) if om.j_blue else None
+    r.spectrum_v = np.zeros(B + 2) if om.n_virtual > 0 else None
     r.status = np.zeros(count, dtype=np.int32)
     r.nu, r.energy = np.zeros(count), np.zeros(count)
     r.counters = np.zeros((count, NCOUNT), dtype=np.uint64)
