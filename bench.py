@@ -22,6 +22,10 @@ models, a captured CUDA graph, autotuned launch shape) is timed against the
 plain per-model binary64 path on the same models, seeds and packet counts;
 the metric is models/s (models completed with all 10 iterations per second).
 
+``--workload spectrum``: the spectrum iteration with virtual packets (N_v = 3)
+on the same model -- transport time with and without them, and the noise per
+spectral bin of both spectra over 8 seeds.
+
 ``--workload serve [--precision mixed|fp64] [--rate R]``: continuous-batching
 service.  Requests arrive as a Poisson process (R = 50 models/s by default)
 for 70 s; each is one model of the batched workload's distribution with
@@ -602,13 +606,84 @@ def run_serve(args):
     return 0
 
 
+def run_spectrum(args):
+    """The spectrum iteration with virtual packets (Sect. 2.9).  Cost: the
+    500k-line downbranch model after 3 iterations of the loop, 1e6 packets,
+    N_v = 3, tau_v cut 30, transport time with and without v-packets (that
+    model escapes almost only below its line list, so its optical spectrum is
+    empty).  Noise: the 2000-line scatter model, 1e5 packets, 8 seeds, the
+    relative spread per spectral bin of the r-packet and v-packet spectra."""
+    import torch
+    from paper_1401_5469_gb300 import mc, synth
+    torch.cuda.set_device(0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    spec = synth.downbranch_model(j_blue=False)
+    N, nv, cut = spec.n_packets, 3, 30.0
+    m = mc.Model(spec)
+    m.set_plasma()
+    for it in range(3):
+        m.run_iteration(spec.seed, it, N, spec.t_inner)
+        mc.mc_update_radiation_field(m.h, None, None)
+    t_rad, w, _ = m.plasma()
+    m.set_plasma(t_rad, w)  # the same plasma state for both spectrum iterations
+    m.run_iteration(spec.seed, 3, N, spec.t_inner)
+    plain_ms = float(m.timing()[1])
+    m.set_virtual_packets(nv, cut)
+    m.run_iteration(spec.seed, 3, N, spec.t_inner)
+    virt_ms = float(m.timing()[1])
+    st = m.spectrum()[1]
+    n_v = nv * (N + st["line_interactions"] + st["e_scatters"])
+    sp = m.spectrum()[0]
+    below = float(sp[spec.spec_bins] / max(sp.sum(), 1e-300))
+    m.close()
+
+    sc = synth.scatter_model(n_packets=100_000)
+    ms = mc.Model(sc)
+    ms.set_plasma(tau=sc.tau)
+    ms.set_virtual_packets(nv)
+    r_sp, v_sp = [], []
+    for k in range(8):
+        ms.run_iteration(5469 + k, 0, sc.n_packets, sc.t_inner)
+        r_sp.append(ms.spectrum()[0][:sc.spec_bins])
+        v_sp.append(ms.virtual_spectrum()[:sc.spec_bins])
+    sc_ms = float(ms.timing()[1])
+    ms.close()
+    clk = clocks.stop()
+    r_sp, v_sp = np.array(r_sp), np.array(v_sp)
+    out = {}
+    for name, g in (("fine_1000_bins", 1), ("coarse_100_bins", 10)):
+        rr = r_sp.reshape(8, -1, g).sum(axis=2)
+        vv = v_sp.reshape(8, -1, g).sum(axis=2)
+        mean_r = rr.mean(axis=0)
+        pop = mean_r > 0.01 * mean_r.max()  # bins above 1% of the peak
+        nr = rr[:, pop].std(axis=0, ddof=1) / rr[:, pop].mean(axis=0)
+        nvv = vv[:, pop].std(axis=0, ddof=1) / vv[:, pop].mean(axis=0)
+        wgt = mean_r[pop] / mean_r[pop].sum()
+        out[name] = {"bins": int(pop.sum()), "r_noise_median": float(np.median(nr)),
+                     "v_noise_median": float(np.median(nvv)),
+                     "noise_ratio_median": float(np.median(nr / nvv)),
+                     "noise_ratio_energy_weighted": float(np.sum(wgt * nr) / np.sum(wgt * nvv))}
+    line = {"metric": "virtual packets/s", "value": n_v / (1e-3 * virt_ms), "unit": "v-packets/s",
+            "n_gpus": 1, "steps": 1, "warmup": 3, "ms_per_step": virt_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "spectrum-iteration-downbranch-500k-lines-1e6-packets-Nv3",
+                       "n_virtual": nv, "tau_v_max": cut, "packets": N},
+            "transport_ms": {"without_virtual": plain_ms, "with_virtual": virt_ms},
+            "virtual_packets": n_v, "escaped_energy_below_line_list": below,
+            "spectrum_noise_scatter_model_1e5_packets_8_seeds": out,
+            "scatter_model_spectrum_iteration_ms": sc_ms, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="downbranch", choices=["downbranch", "batched", "serve"])
+    ap.add_argument("--workload", default="downbranch", choices=["downbranch", "batched", "serve", "spectrum"])
     ap.add_argument("--models", type=int, default=256)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--rate", type=float, default=50.0)
@@ -620,6 +695,8 @@ def main():
         return run_batched(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "spectrum":
+        return run_spectrum(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -233,6 +233,28 @@ mc_status mc_read_transport_phases(mc_model *m, float *ms);
 /* Number of kernels this model has launched since creation. */
 mc_status mc_launch_count(const mc_model *m, uint64_t *count);
 
+/* Virtual packets (Sect. 2.9, Eqs. 19-21) in the following iterations: at
+ * injection and after every interaction each packet spawns n_virtual
+ * v-packets with directions uniform in (mu_min, 1], mu_min = -sqrt(1 -
+ * (r_inner/r)^2), comoving energy E (1 - mu_min) / (2 n_virtual) (after an
+ * interaction) or E 2 mu_v / n_virtual (at injection); each flies to the
+ * outer boundary without interacting and adds exp(-tau_v) times its lab-frame
+ * energy to the bin of its lab frequency in the v-spectrum.  tau_v_max > 0
+ * drops a v-packet once tau_v exceeds it (changing the spectrum by less than
+ * exp(-tau_v_max) of that packet); 0 keeps every v-packet.  The v-packets
+ * draw from their own Philox stream, so the r-packets' histories, estimators
+ * and spectrum are unchanged.  n_virtual = 0 turns them off.  Binary64
+ * models only (MC_ERR_UNSUPPORTED otherwise); n_virtual <= 1024.
+ * Errors: MC_ERR_INVALID_ARG, MC_ERR_UNSUPPORTED, MC_ERR_OOM. */
+mc_status mc_set_virtual_packets(mc_model *m, uint32_t n_virtual, double tau_v_max);
+
+/* v-spectrum of the last iteration: spectrum_v[spec_bins + 2] receives the
+ * raw sums of E_lab exp(-tau_v) (erg) per bin, then the below-range and
+ * above-range sums (the layout of mc_read_spectrum).  Synchronises the
+ * model's stream.  Errors: MC_ERR_INVALID_ARG, MC_ERR_NOT_READY (no run, or
+ * virtual packets off). */
+mc_status mc_read_virtual_spectrum(mc_model *m, double *spectrum_v);
+
 /* Device views of the model's estimator buffers, for callers that combine
  * the partial sums of several packet ranges in place (a sum all-reduce across
  * processes, one GPU each, each having run mc_run_iteration_range on its own

@@ -512,6 +512,10 @@ mc_status model_prepare(mc_model *m, cudaStream_t st, bool events) {
     e = cudaMemsetAsync(m->est_fix, 0, 2 * static_cast<size_t>(m->S) * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(m, e, "zero fixed-point estimators");
   }
+  if (m->spectrum_v && m->n_virtual) {
+    e = cudaMemsetAsync(m->spectrum_v, 0, (static_cast<size_t>(m->run.spec_bins) + 2) * sizeof(double), st);
+    if (e != cudaSuccess) return cuda_fail(m, e, "zero virtual-packet spectrum");
+  }
   return MC_OK;
 }
 
@@ -536,6 +540,9 @@ void model_fill_transport(const mc_model *m, TransportParams &p, uint64_t seed, 
   p.nu = m->nu; p.tau = m->tau; p.tau32 = m->tau32;
   p.line_row = m->line_row; p.dbr_offset = m->dbr_offset; p.dbr_line = m->dbr_line; p.dbr_cdf = m->dbr_cdf;
   p.j_est = m->j_est; p.nu_bar = m->nu_bar; p.j_blue = m->j_blue; p.spectrum = m->spectrum;
+  p.n_virtual = static_cast<int32_t>(m->n_virtual);
+  p.tau_v_max = m->tau_v_max;
+  p.spectrum_v = m->n_virtual ? m->spectrum_v : nullptr;
   p.stats = m->counters;
   p.work_counter = m->counters + kNStats;
   p.flags = m->counters + kNStats + 1;
@@ -654,6 +661,33 @@ mc_status mc_read_spectrum(mc_model *m, double *spectrum, mc_packet_stats *stats
   }
   if (c[kNStats + 1]) return fail(m, MC_ERR_TIMEOUT, "transport kernel stopped at its deadline");
   return c[kStCapped] ? MC_WARN_CAPPED : MC_OK;
+}
+
+mc_status mc_set_virtual_packets(mc_model *m, uint32_t n_virtual, double tau_v_max) {
+  if (!m) return MC_ERR_INVALID_ARG;
+  if (m->run.precision != MC_PRECISION_FP64)
+    return fail(m, MC_ERR_UNSUPPORTED, "virtual packets run in the binary64 kernel");
+  if (n_virtual > 1024) return fail(m, MC_ERR_INVALID_ARG, "at most 1024 virtual packets per launch");
+  if (!(tau_v_max >= 0.0) || !std::isfinite(tau_v_max))
+    return fail(m, MC_ERR_INVALID_ARG, "tau_v_max must be finite and >= 0");
+  if (n_virtual && !m->spectrum_v) {
+    if (!alloc_n(m, &m->spectrum_v, static_cast<size_t>(m->run.spec_bins) + 2))
+      return fail(m, MC_ERR_OOM, "device allocation failed");
+  }
+  m->n_virtual = n_virtual;
+  m->tau_v_max = tau_v_max;
+  return MC_OK;
+}
+
+mc_status mc_read_virtual_spectrum(mc_model *m, double *spectrum_v) {
+  if (!m || !spectrum_v) return MC_ERR_INVALID_ARG;
+  if (!m->have_run) return fail(m, MC_ERR_NOT_READY, "no run yet");
+  if (!m->spectrum_v || !m->n_virtual) return fail(m, MC_ERR_NOT_READY, "virtual packets are off");
+  cudaError_t e = cudaMemcpyAsync(spectrum_v, m->spectrum_v, (m->run.spec_bins + 2) * sizeof(double),
+                                  cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(m, e, "read virtual spectrum");
+  return MC_OK;
 }
 
 mc_status mc_read_packets(mc_model *m, uint64_t first, uint64_t count, int32_t *status, double *nu,

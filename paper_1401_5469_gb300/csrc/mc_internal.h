@@ -86,6 +86,10 @@ struct TransportParams {
   unsigned long long timeout_ns;     // 0 = none
   unsigned long long *flags;         // [0] deadline hit, [1] work queue empty (ns),
                                      // [2] last warp done (ns), [3] first warp start (ns)
+  // virtual packets (Sect. 2.9; binary64 kernel)
+  int32_t n_virtual;                 // N_v per launch of an r-packet trajectory, 0 = off
+  double tau_v_max;                  // > 0: a v-packet is dropped once tau_v exceeds it
+  double *spectrum_v;                // [bins + 2] sums of E_lab exp(-tau_v) (Eq. 21)
 };
 
 constexpr int kNCounterSlots = kNStats + 5;  // stats, work counter, flags[4]

@@ -49,6 +49,9 @@ struct mc_model {
   uint8_t *meta = nullptr;
   double *norm = nullptr;
   double *j_est = nullptr, *nu_bar = nullptr, *j_blue = nullptr, *spectrum = nullptr;
+  double *spectrum_v = nullptr;  // [bins + 2] virtual-packet spectrum (allocated on first use)
+  uint32_t n_virtual = 0;
+  double tau_v_max = 0.0;
   unsigned long long *counters = nullptr;  // stats [kNStats], work counter, flags
   double *planck_cdf = nullptr;
   int32_t *rec_status = nullptr;

@@ -135,8 +135,8 @@ __device__ __forceinline__ bool inside_shell(double pp, double q, double l, bool
 // Injection at the inner boundary, Sect. 2.4: Planck-sampled comoving
 // frequency (Carter & Cashwell series method), mu = sqrt(z), equal comoving
 // energy (Eq. 10), lab-frame values by the first-order Doppler factor.
-__device__ __forceinline__ void inject(const TransportParams &p, const double *planck, double x0,
-                                       double x0sq, Packet &pk, DrawStream &ds) {
+__device__ __forceinline__ double inject(const TransportParams &p, const double *planck, double x0,
+                                         double x0sq, Packet &pk, DrawStream &ds) {
   const double z0 = ds.closed0();
   const double z1 = ds.open0(), z2 = ds.open0(), z3 = ds.open0(), z4 = ds.open0();
   int l = 1;
@@ -159,6 +159,87 @@ __device__ __forceinline__ void inject(const TransportParams &p, const double *p
   pk.next_line = first_redward(p.nu, p.L, nu_cmf);
 #pragma unroll
   for (int c = 0; c < kNCounters; ++c) pk.cnt[c] = 0u;
+  return nu_cmf;
+}
+
+// Spectrum bin of a lab frequency; below the range -> bins, above (or NaN)
+// -> bins + 1 (Sect. 2.9 direct binning).
+__device__ __forceinline__ int spectrum_bin(const TransportParams &p, double nu_lab) {
+  if (nu_lab < p.spec_lo) return p.spec_bins;
+  const double t = (nu_lab - p.spec_lo) / p.spec_dnu;
+  return (t >= 0.0 && t < static_cast<double>(p.spec_bins)) ? static_cast<int>(floor(t)) : p.spec_bins + 1;
+}
+
+// ---- virtual packets (Sect. 2.9, Eqs. 19-21)
+// Whenever an r-packet is about to start a trajectory (injection, or after an
+// interaction), N_v v-packets leave its position with its comoving frequency
+// and energy, in directions mu_v = mu_min + (1 - mu_min) z, z in (0, 1], with
+// mu_min = -sqrt(1 - (x_in / x)^2) so that none meets the inner boundary.  A
+// v-packet never interacts: it collects the Sobolev depths of the lines it
+// passes and the electron-scattering depth kappa' D l of each segment (D at
+// the segment start) on its way out, and adds exp(-tau_v) times its lab
+// energy to the bin of its lab frequency.  Comoving energies: E (1 - mu_min)
+// / (2 N_v) after an interaction (Eq. 19), E 2 mu_v / N_v at injection
+// (Eq. 20).  Draws come from Philox stream 1 (counter word 3 = 1), the v-draw
+// index counting on across the packet's launches, so the r-packet's own
+// draws are untouched.
+
+struct VirtualLaunch {
+  double x, r2, nu_cmf, e_cmf;  // radius (units of c t_exp), its square, comoving nu and E
+  int32_t shell, next_line;
+  uint32_t pid, first_draw;
+  bool injection;
+};
+
+__device__ __forceinline__ double vdraw_open0(const TransportParams &p, uint32_t pid, uint32_t d) {
+  const uint4 o = philox4x32_10(make_uint4(d >> 1, pid, p.iteration, 1u), p.key0, p.key1);
+  const unsigned long long u = (d & 1u) ? DrawStream::u53_of(o.z, o.w) : DrawStream::u53_of(o.x, o.y);
+  return __ull2double_rn(u + 1ull) * 0x1.0p-53;
+}
+
+// Kept out of line: it runs only in the spectrum iteration and must not add
+// registers to the transport loop.
+__device__ __noinline__ void spawn_virtual(const TransportParams &p, const double *sh, VirtualLaunch v) {
+  const int32_t S = p.S, L = p.L, nv = p.n_virtual;
+  const double *s_xi2 = sh, *s_xo2 = sh + S, *s_kap = sh + 4 * S;
+  const double ri = sh[2 * S] / v.x;  // x_in[0] / x
+  const double arg = 1.0 - ri * ri;
+  const double mu_min = -sqrt(rawkey(arg) > 0 ? arg : 0.0);
+  const long long *nub = reinterpret_cast<const long long *>(p.nu);
+  const bool cut = rawkey(p.tau_v_max) > 0;
+  for (int32_t i = 0; i < nv; ++i) {
+    const double mu_v = mu_min + (1.0 - mu_min) * vdraw_open0(p, v.pid, v.first_draw + i);
+    double pc = v.x * mu_v;
+    const double D = 1.0 - pc;
+    const double q = max0(fma(-pc, pc, v.r2));
+    const double e_v = v.injection ? (v.e_cmf * (2.0 * mu_v)) / nv : (v.e_cmf * (1.0 - mu_min)) / (2.0 * nv);
+    const double nu_lab = v.nu_cmf / D;
+    double tau = 0.0;
+    int32_t s = v.shell, j = v.next_line;
+    bool out = false;
+    for (;;) {
+      const double xi2 = s_xi2[s], xo2 = s_xo2[s];
+      const bool inner = strictly_negative(pc) && rawkey(q) <= rawkey(xi2);
+      const double p_exit = shell_exit(q, inner, xi2, xo2);
+      // Sobolev points before the exit: nu_j > nu_lab (1 - p_exit)
+      const long long key_exit = rawkey(nu_lab * (1.0 - p_exit));
+      const double *tau_s = p.tau + static_cast<size_t>(s) * static_cast<size_t>(L);
+      bool over = false;
+      while (j < L && __ldg(nub + j) > key_exit) {
+        tau += __ldg(tau_s + j);
+        ++j;
+        if (cut && rawkey(tau) > rawkey(p.tau_v_max)) { over = true; break; }
+      }
+      if (over) break;
+      tau += (s_kap[s] * (1.0 - pc)) * max0(p_exit - pc);
+      if (cut && rawkey(tau) > rawkey(p.tau_v_max)) break;
+      pc = p_exit;
+      s += inner ? -1 : 1;
+      if (s >= S) { out = true; break; }
+      if (s < 0) break;  // met the inner boundary (only by rounding)
+    }
+    if (out) atomicAdd(p.spectrum_v + spectrum_bin(p, nu_lab), (e_v / D) * exp(-tau));
+  }
 }
 
 template <int MODE, bool JB, bool REC>
@@ -190,6 +271,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
   wd.init(reinterpret_cast<unsigned long long *>(sh + kShellArrays * S) +
           2 * kWarpDraws * (threadIdx.x >> 5));
   bool alive = false, finished = false;
+  uint32_t vdraws = 0u;  // v-packet draws used by this lane's packet
   unsigned long long n_esc = 0, n_reab = 0, n_cap = 0, n_seg = 0, n_chk = 0, n_res = 0, n_lint = 0,
                      n_esca = 0, n_shell = 0;
   int32_t acc_s = -1;
@@ -211,8 +293,13 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         if (id < p.n_packets) {
           pk.pid = static_cast<uint32_t>(p.first_packet + id);
           ds.init(p.key0, p.key1, pk.pid, p.iteration);
-          inject(p, p.planck_cdf, x0, x0sq, pk, ds);
+          const double nu_cmf0 = inject(p, p.planck_cdf, x0, x0sq, pk, ds);
           alive = true;
+          vdraws = 0u;
+          if (p.n_virtual) {
+            spawn_virtual(p, sh, VirtualLaunch{x0, x0sq, nu_cmf0, p.e_cmf, 0, pk.next_line, pk.pid, 0u, true});
+            vdraws = static_cast<uint32_t>(p.n_virtual);
+          }
         } else {
           finished = true;
           atomicCAS(p.flags + 1, 0ull, global_ns());
@@ -414,6 +501,10 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         pk.inv_nu = inv_nu_c * D2;
         pk.inv_D = iD2;
         pk.have_inv_D = true;
+        if (p.n_virtual) {
+          spawn_virtual(p, sh, VirtualLaunch{xn, r2n, nu_c, e_c, s, pk.next_line, pk.pid, vdraws, false});
+          vdraws += static_cast<uint32_t>(p.n_virtual);
+        }
       }
     }
     if (status != 0) {
@@ -426,17 +517,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       n_lint += pk.cnt[3];
       n_esca += pk.cnt[4];
       n_shell += pk.cnt[5];
-      if (status == 1) {
-        // bin index; underflow -> bins, overflow (or NaN) -> bins + 1
-        int b;
-        if (pk.nu_lab < p.spec_lo) b = p.spec_bins;
-        else {
-          const double t = (pk.nu_lab - p.spec_lo) / p.spec_dnu;
-          b = (t >= 0.0 && t < static_cast<double>(p.spec_bins)) ? static_cast<int>(floor(t))
-                                                                   : p.spec_bins + 1;
-        }
-        atomicAdd(p.spectrum + b, pk.e_lab);
-      }
+      if (status == 1) atomicAdd(p.spectrum + spectrum_bin(p, pk.nu_lab), pk.e_lab);
       if (REC) {
         p.rec_status[pk.pid - p.first_packet] = status;
         p.rec_nu[pk.pid - p.first_packet] = pk.nu_lab;

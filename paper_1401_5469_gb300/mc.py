@@ -42,7 +42,7 @@ EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_run_iter
             "mc_batch_create", "mc_batch_run_iteration", "mc_batch_synchronize",
             "mc_batch_read_timing", "mc_batch_last_error_message", "mc_batch_destroy",
             "mc_batch_set_launch", "mc_batch_get_launch", "mc_batch_autotune",
-            "mc_device_estimators")
+            "mc_device_estimators", "mc_set_virtual_packets", "mc_read_virtual_spectrum")
 
 MC_ORDER_PACKETS, MC_ORDER_WORK, MC_ORDER_GIVEN = 0, 1, 2
 
@@ -192,6 +192,10 @@ def load(build_if_missing: bool = True):
     L.mc_batch_last_error_message.argtypes = [vp]
     L.mc_batch_destroy.restype = None
     L.mc_batch_destroy.argtypes = [vp]
+    L.mc_set_virtual_packets.restype = i32
+    L.mc_set_virtual_packets.argtypes = [vp, u32, d]
+    L.mc_read_virtual_spectrum.restype = i32
+    L.mc_read_virtual_spectrum.argtypes = [vp, vp]
     L.mc_device_estimators.restype = i32
     L.mc_device_estimators.argtypes = [vp, P(mc_estimator_views)]
     L.mc_batch_set_launch.restype = i32
@@ -420,6 +424,16 @@ class Model:
         jb = np.zeros((self.S, self.L)) if j_blue else None
         mc_read_estimators(self.h, j, nb, jb, norm)
         return j, nb, jb, norm
+
+    def set_virtual_packets(self, n_virtual: int, tau_v_max: float = 0.0):
+        """Virtual packets (Sect. 2.9) in the following iterations (0: off)."""
+        return _check(load().mc_set_virtual_packets(self.h, int(n_virtual), float(tau_v_max)), self.h)
+
+    def virtual_spectrum(self):
+        """Raw v-spectrum sums of the last iteration ([bins + 2])."""
+        sp = np.zeros(self.bins + 2)
+        _check(load().mc_read_virtual_spectrum(self.h, _p(sp)), self.h)
+        return sp
 
     def device_estimators(self):
         """Torch views (no copy) of the model's device estimator buffers:
