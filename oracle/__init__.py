@@ -77,6 +77,8 @@ class _Model(C.Structure):
         ("delta_t", C.c_double),
         ("n_virtual", C.c_int32),
         ("tau_v_max", C.c_double),
+        ("ma_jump_p", C.c_void_p), ("ma_jump_offset", C.c_void_p), ("ma_jump_target", C.c_void_p),
+        ("ma_jump_cdf", C.c_void_p),
     ]
 
 
@@ -126,6 +128,7 @@ def lib():
             L.orc_run_traced.restype = i32
             L.orc_run_traced.argtypes = [C.POINTER(_Model), u64, u32, u64, d, u64, u64,
                                          C.POINTER(_Result), C.POINTER(_Trace)]
+            L.orc_macroatom_walks.argtypes = [C.POINTER(_Model), i32, u64, i64, vp, vp]
             L.orc_virtual_tau.restype = d
             L.orc_virtual_tau.argtypes = [C.POINTER(_Model), d, d, i32, d, i32]
             L.orc_inject_packets.restype = i32
@@ -216,12 +219,18 @@ class OracleModel:
         self.line_mode = int(spec.line_mode)
         self.j_blue = int(bool(spec.j_blue))
         self.line_row = None
-        if self.line_mode == 1:
+        self.ma_jump_p = self.ma_jump_offset = self.ma_jump_target = self.ma_jump_cdf = None
+        if self.line_mode >= 1:
             self.line_row = (np.asarray(spec.ion, np.int64) * int(spec.n_levels)
                              + np.asarray(spec.upper, np.int64)).astype(np.int32)
             self.dbr_offset = np.ascontiguousarray(spec.dbr_offset, dtype=np.uint32)
             self.dbr_line = np.ascontiguousarray(spec.dbr_line, dtype=np.uint32)
             self.dbr_cdf = _f64(spec.dbr_cdf)
+            if self.line_mode == 2:
+                self.ma_jump_p = _f64(spec.ma_jump_p)
+                self.ma_jump_offset = np.ascontiguousarray(spec.ma_jump_offset, dtype=np.uint32)
+                self.ma_jump_target = np.ascontiguousarray(spec.ma_jump_target, dtype=np.int32)
+                self.ma_jump_cdf = _f64(spec.ma_jump_cdf)
         else:
             self.dbr_offset = self.dbr_line = self.dbr_cdf = None
         self.max_segments = int(max_segments)
@@ -250,7 +259,9 @@ class OracleModel:
             dbr_offset=_p(self.dbr_offset), dbr_line=_p(self.dbr_line), dbr_cdf=_p(self.dbr_cdf),
             j_blue=self.j_blue, spec_bins=int(s.spec_bins), spec_nu_lo=float(s.spec_nu_lo),
             spec_nu_hi=float(s.spec_nu_hi), max_segments=self.max_segments, delta_t=self.delta_t,
-            n_virtual=self.n_virtual, tau_v_max=self.tau_v_max)
+            n_virtual=self.n_virtual, tau_v_max=self.tau_v_max,
+            ma_jump_p=_p(self.ma_jump_p), ma_jump_offset=_p(self.ma_jump_offset),
+            ma_jump_target=_p(self.ma_jump_target), ma_jump_cdf=_p(self.ma_jump_cdf))
 
 
 class OracleResult:
@@ -336,6 +347,15 @@ def virtual_tau(om: OracleModel, x: float, mu: float, shell: int, nu_lab: float,
     or exceeds the model's tau_v_max."""
     return float(lib().orc_virtual_tau(C.byref(om.c), float(x), float(mu), int(shell), float(nu_lab),
                                        int(next_line)))
+
+
+def macroatom_walks(om: OracleModel, row: int, seed: int, n: int):
+    """n macro-atom walks activated in level `row` (Sect. 2.5), walk i drawing
+    from packet i's stream: (emitting line, number of internal jumps)."""
+    line = np.zeros(n, dtype=np.int32)
+    jumps = np.zeros(n, dtype=np.uint32)
+    lib().orc_macroatom_walks(C.byref(om.c), int(row), int(seed), int(n), _p(line), _p(jumps))
+    return line, jumps
 
 
 def downbranch_pick(om: OracleModel, row: int, z: float) -> int:

@@ -274,7 +274,7 @@ typedef struct {
     int32_t n_lines;
     const double *nu;                      /* [L] Hz, strictly descending */
     const double *tau;                     /* [S*L] shell-major Sobolev depths */
-    int32_t line_mode;                     /* 0 scatter, 1 downbranch */
+    int32_t line_mode;                     /* 0 scatter, 1 downbranch, 2 macro atom */
     const int32_t *line_row;               /* [L] branching row of each line (downbranch) */
     const uint32_t *dbr_offset;            /* [rows+1] */
     const uint32_t *dbr_line;              /* [nnz] emitting line of each entry */
@@ -286,6 +286,11 @@ typedef struct {
     double delta_t;                        /* s */
     int32_t n_virtual;                     /* N_v virtual packets per launch (Sect. 2.9), 0 = off */
     double tau_v_max;                      /* drop a v-packet once tau_v exceeds this (0 = never) */
+    /* macro-atom internal jumps (line_mode 2), rows as the branching table */
+    const double *ma_jump_p;               /* [rows] probability that the level jumps */
+    const uint32_t *ma_jump_offset;        /* [rows+1] */
+    const int32_t *ma_jump_target;         /* [n] level (row) jumped to */
+    const double *ma_jump_cdf;             /* [n] cumulative target probability */
 } orc_model;
 
 typedef struct {
@@ -368,6 +373,44 @@ static int32_t downbranch_pick(const orc_model *m, int32_t row, double z)
 }
 
 int32_t orc_downbranch_pick(const orc_model *m, int32_t row, double z) { return downbranch_pick(m, row, z); }
+
+/* Macro atom (Sect. 2.5, mode macroatom): activated in a level (row), the
+ * atom makes internal transitions -- from its current level it jumps with
+ * that level's probability ma_jump_p, to the target the level's jump CDF
+ * picks -- until it deactivates through the current level's branching row
+ * (the downbranch choice).  Draws, in order: per step one to decide whether
+ * to jump, one for the target if it jumps; then one for the emitting line.
+ * After ORC_MA_MAX_STEPS jumps the atom deactivates without the decision. */
+#define ORC_MA_MAX_STEPS 1024
+static int32_t macroatom_emit(const orc_model *m, int32_t row, orc_rng *r, uint32_t *jumps)
+{
+    uint32_t n = 0;
+    while (n < ORC_MA_MAX_STEPS) {
+        double za = rng_closed0(r);
+        if (!(za < m->ma_jump_p[row])) break;
+        double zb = rng_closed0(r);
+        uint32_t b = m->ma_jump_offset[row], e = m->ma_jump_offset[row + 1];
+        int32_t next = m->ma_jump_target[e - 1];
+        for (uint32_t k = b; k < e; ++k) {
+            if (zb < m->ma_jump_cdf[k]) { next = m->ma_jump_target[k]; break; }
+        }
+        row = next;
+        n += 1;
+    }
+    if (jumps) *jumps = n;
+    return downbranch_pick(m, row, rng_closed0(r));
+}
+
+/* n walks from level row, walk i drawing from the r-packet stream of packet i
+ * (seed, iteration 0): emitting line and number of jumps of each. */
+void orc_macroatom_walks(const orc_model *m, int32_t row, uint64_t seed, int64_t n, int32_t *line, uint32_t *jumps)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        orc_rng r;
+        rng_init(&r, seed, 0u, (uint32_t)i, 0u);
+        line[i] = macroatom_emit(m, row, &r, jumps ? &jumps[i] : NULL);
+    }
+}
 
 /* ------------------------------------------------------------ one packet */
 typedef struct {
@@ -644,6 +687,7 @@ static void transport(const orc_model *m, const orc_geom *g, orc_rng *r, orc_rng
             const double e_c = pk->e_lab * D1;
             int32_t emit = j;
             if (m->line_mode == 1) emit = downbranch_pick(m, m->line_row[j], rng_closed0(r));
+            else if (m->line_mode == 2) emit = macroatom_emit(m, m->line_row[j], r, NULL);
             const double mu2 = -1.0 + 2.0 * rng_closed0(r);
             const double D2 = 1.0 - mu2 * xn;
             if (trace) {
@@ -738,7 +782,10 @@ static int valid_model(const orc_model *m)
 {
     if (m->n_shells <= 0 || m->n_lines < 0 || m->spec_bins <= 0) return 0;
     if (!m->v_inner || !m->v_outer || !m->n_e || !m->tau || (m->n_lines > 0 && !m->nu)) return 0;
-    if (m->line_mode == 1 && (!m->line_row || !m->dbr_offset || !m->dbr_line || !m->dbr_cdf)) return 0;
+    if (m->line_mode < 0 || m->line_mode > 2) return 0;
+    if (m->line_mode >= 1 && (!m->line_row || !m->dbr_offset || !m->dbr_line || !m->dbr_cdf)) return 0;
+    if (m->line_mode == 2 && (!m->ma_jump_p || !m->ma_jump_offset || !m->ma_jump_target || !m->ma_jump_cdf))
+        return 0;
     return 1;
 }
 

@@ -68,7 +68,12 @@ class ModelSpec:
     dbr_offset: Optional[np.ndarray] = None
     dbr_line: Optional[np.ndarray] = None
     dbr_cdf: Optional[np.ndarray] = None
-    line_mode: int = 0          # 0 scatter, 1 downbranch
+    # macro-atom internal jumps (line_mode 2), rows as the branching table
+    ma_jump_p: Optional[np.ndarray] = None       # [rows] probability of a jump from the level
+    ma_jump_offset: Optional[np.ndarray] = None  # [rows + 1] CSR over the rows
+    ma_jump_target: Optional[np.ndarray] = None  # [n] row jumped to
+    ma_jump_cdf: Optional[np.ndarray] = None     # [n] cumulative target probability (row ends at 1)
+    line_mode: int = 0          # 0 scatter, 1 downbranch, 2 macro-atom
     j_blue: bool = False
     spec_bins: int = 1000
     spec_nu_lo: float = SPEC_NU_LO
@@ -176,6 +181,53 @@ def downbranch_table(rng, ion, upper, n_ions: int, n_levels: int):
     is_last = np.arange(row.shape[0]) == (end - 1)
     cdf[is_last] = 1.0
     return offset, order.astype(np.uint32), cdf
+
+
+def macroatom_table(rng, dbr_offset, n_ions: int, n_levels: int, p_jump_max: float = 0.5,
+                    n_targets: int = 8):
+    """Synthetic macro-atom internal transitions (the paper uses radiative
+    rates it does not list).  Every level that can deactivate (its branching
+    row is not empty) jumps with probability p ~ U(0, p_jump_max) to one of up
+    to n_targets other such levels of the same ion, with Dirichlet(1,...,1)
+    target weights; otherwise it deactivates through its branching row.  Only
+    levels that can deactivate are jump targets, so every walk ends.
+    """
+    n_rows = n_ions * n_levels
+    counts = np.diff(np.asarray(dbr_offset, dtype=np.int64))
+    p = np.zeros(n_rows)
+    offset = np.zeros(n_rows + 1, dtype=np.uint32)
+    targets, cdfs = [], []
+    for ion in range(n_ions):
+        rows = np.arange(ion * n_levels, (ion + 1) * n_levels)
+        live = rows[counts[rows] > 0]
+        for r in rows:
+            if counts[r] > 0 and live.size > 1:
+                others = live[live != r]
+                k = min(n_targets, others.size)
+                t = np.sort(rng.choice(others, size=k, replace=False))
+                w = -np.log(1.0 - rng.random(size=k))
+                c = np.cumsum(w) / w.sum()
+                c[-1] = 1.0
+                targets.append(t)
+                cdfs.append(c)
+                p[r] = rng.uniform(0.0, p_jump_max)
+                offset[r + 1] = offset[r] + k
+            else:
+                offset[r + 1] = offset[r]
+    target = np.concatenate(targets).astype(np.int32) if targets else np.zeros(0, np.int32)
+    cdf = np.concatenate(cdfs) if cdfs else np.zeros(0)
+    return p, offset, target, cdf
+
+
+def macroatom_model(p_jump_max: float = 0.5, **kw) -> ModelSpec:
+    """The downbranch model in macro-atom mode (line_mode 2): the same atomic
+    data and branching rows plus synthetic internal jumps."""
+    spec = downbranch_model(line_mode=2, **kw)
+    rng = np.random.default_rng(int(kw.get("seed", 1401)) + 7)
+    (spec.ma_jump_p, spec.ma_jump_offset, spec.ma_jump_target,
+     spec.ma_jump_cdf) = macroatom_table(rng, spec.dbr_offset, spec.n_ions, spec.n_levels, p_jump_max)
+    spec.name = "macroatom"
+    return spec
 
 
 # ---------------------------------------------------------------- presets

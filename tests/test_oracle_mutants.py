@@ -68,6 +68,15 @@ MUTANTS = [
     ("v-packet directions only outward", "const double mu_min = -sqrt(arg);",
      "const double mu_min = sqrt(arg);", 1,
      "tests/test_oracle_virtual.py::test_scattering_model_v_and_r_spectra_agree_and_v_is_less_noisy"),
+    ("macro atom deactivates from the activated level", "        row = next;\n",
+     "        (void)next;\n", 1,
+     "tests/test_oracle_macroatom.py::test_walks_match_the_absorbing_markov_chain"),
+    ("macro-atom jump decision inverted", "if (!(za < m->ma_jump_p[row])) break;",
+     "if (za < m->ma_jump_p[row]) break;", 1,
+     "tests/test_oracle_macroatom.py::test_walks_match_the_absorbing_markov_chain"),
+    ("macro-atom jump target off by one", "if (zb < m->ma_jump_cdf[k]) { next = m->ma_jump_target[k]; break; }",
+     "if (zb < m->ma_jump_cdf[k]) { next = m->ma_jump_target[k > b ? k - 1 : k]; break; }", 1,
+     "tests/test_oracle_macroatom.py::test_walks_match_the_absorbing_markov_chain"),
 ]
 
 
