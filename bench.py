@@ -26,6 +26,9 @@ the metric is models/s (models completed with all 10 iterations per second).
 on the same model -- transport time with and without them, and the noise per
 spectral bin of both spectra over 8 seeds.
 
+``--workload macroatom``: the same model with macro-atom line interactions
+(synthetic internal jumps) against downbranch, per-iteration transport time.
+
 ``--workload serve [--precision mixed|fp64] [--rate R]``: continuous-batching
 service.  Requests arrive as a Poisson process (R = 50 models/s by default)
 for 70 s; each is one model of the batched workload's distribution with
@@ -677,13 +680,54 @@ def run_spectrum(args):
     return 0
 
 
+def run_macroatom(args):
+    """Macro-atom vs downbranch line interactions (Sect. 2.5) on the 500k-line,
+    1e6-packet model (the same lines and branching rows; macro-atom mode adds
+    synthetic internal jumps), binary64, 1 warm-up and 3 timed iterations of
+    the loop each."""
+    import torch
+    from paper_1401_5469_gb300 import mc, synth
+    torch.cuda.set_device(0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = {}
+    for name, spec in (("downbranch", synth.downbranch_model(j_blue=False)),
+                       ("macroatom", synth.macroatom_model(j_blue=False))):
+        N = spec.n_packets
+        m = mc.Model(spec)
+        m.set_plasma()
+        ms, inter = [], []
+        for it in range(4):
+            m.run_iteration(spec.seed, it, N, spec.t_inner)
+            mc.mc_update_radiation_field(m.h, None, None)
+            if it:
+                ms.append(float(m.timing()[1]))
+                st = m.spectrum()[1]
+                inter.append(st["line_interactions"] + st["e_scatters"])
+        m.close()
+        t = float(np.median(ms))
+        res[name] = {"transport_ms_median": t, "packets_per_s": N / (1e-3 * t),
+                     "interactions_per_iteration": float(np.mean(inter)),
+                     "interactions_per_s": float(np.mean(inter)) / (1e-3 * t)}
+    clk = clocks.stop()
+    ratio = res["macroatom"]["transport_ms_median"] / res["downbranch"]["transport_ms_median"]
+    line = {"metric": "packets/s", "value": res["macroatom"]["packets_per_s"], "unit": "packets/s",
+            "n_gpus": 1, "steps": 3, "warmup": 1, "ms_per_step": res["macroatom"]["transport_ms_median"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "macroatom-vs-downbranch-500k-lines-1e6-packets", "j_blue": False},
+            "modes": res, "macroatom_time_over_downbranch": ratio, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="downbranch", choices=["downbranch", "batched", "serve", "spectrum"])
+    ap.add_argument("--workload", default="downbranch", choices=["downbranch", "batched", "serve", "spectrum", "macroatom"])
     ap.add_argument("--models", type=int, default=256)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--rate", type=float, default=50.0)
@@ -697,6 +741,8 @@ def main():
         return run_serve(args)
     if args.workload == "spectrum":
         return run_spectrum(args)
+    if args.workload == "macroatom":
+        return run_macroatom(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -51,6 +51,9 @@ typedef int32_t mc_status;
 #define MC_LINE_SCATTER 0    /* resonance scattering: re-emit in the absorbing line */
 #define MC_LINE_DOWNBRANCH 1 /* macro atom without internal jumps: re-emit via the
                                 branching table of the activated upper level */
+#define MC_LINE_MACROATOM 2  /* macro atom: internal jumps between the ion's levels
+                                (ma_jump_* tables), then re-emission via the branching
+                                table of the level it deactivates from */
 
 /* Precision modes. */
 #define MC_PRECISION_FP64 0  /* all transport arithmetic in binary64 */
@@ -108,6 +111,18 @@ typedef struct {
     const uint32_t *dbr_line;  /* [nnz] line index of each branch */
     const double *dbr_cdf;     /* [nnz] cumulative branching ratio within the row */
     int32_t lte_excitation;    /* 1: Eq. 4 for every level; 0: dilute-lte (Eq. 5) */
+    /* Macro-atom internal jumps (MC_LINE_MACROATOM, else NULL), rows as the
+     * downbranch table: from level r the atom jumps with probability
+     * ma_jump_p[r] in [0, 1) to a level picked by the CSR row r of
+     * (ma_jump_target, ma_jump_cdf) -- targets are rows with a non-empty
+     * downbranch row, cdf non-decreasing with last == 1, and the row is not
+     * empty when ma_jump_p[r] > 0 -- or deactivates through its downbranch
+     * row.  Draws per step: the jump decision, then the target if it jumps;
+     * then the emitting line.  After 1024 jumps the atom deactivates. */
+    const double *ma_jump_p;          /* [I*K] */
+    const uint32_t *ma_jump_offset;   /* [I*K + 1] */
+    const int32_t *ma_jump_target;    /* [n] */
+    const double *ma_jump_cdf;        /* [n] */
 } mc_atomic_desc;
 
 /* Run options. */

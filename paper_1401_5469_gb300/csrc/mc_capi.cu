@@ -158,8 +158,11 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
     if (j > 0 && !(lines->nu[j] < lines->nu[j - 1]))
       return fail(nullptr, MC_ERR_INVALID_ARG, "line frequencies must be strictly descending");
   }
-  if (run->line_mode != MC_LINE_SCATTER && run->line_mode != MC_LINE_DOWNBRANCH)
+  if (run->line_mode != MC_LINE_SCATTER && run->line_mode != MC_LINE_DOWNBRANCH &&
+      run->line_mode != MC_LINE_MACROATOM)
     return fail(nullptr, MC_ERR_INVALID_ARG, "unknown line_mode");
+  if (run->line_mode == MC_LINE_MACROATOM && run->precision != MC_PRECISION_FP64)
+    return fail(nullptr, MC_ERR_UNSUPPORTED, "macro-atom mode runs in the binary64 kernel");
   if (run->precision != MC_PRECISION_FP64 && run->precision != MC_PRECISION_MIXED)
     return fail(nullptr, MC_ERR_INVALID_ARG, "unknown precision");
   if (run->precision == MC_PRECISION_MIXED && run->line_mode == MC_LINE_DOWNBRANCH &&
@@ -170,10 +173,13 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
   if (run->record_packets && (run->max_packets == 0 || run->max_packets >= (1ull << 32)))
     return fail(nullptr, MC_ERR_INVALID_ARG, "record_packets needs 0 < max_packets < 2^32");
   const bool meta = lines->ion && lines->lower && lines->upper;
-  if (run->line_mode == MC_LINE_DOWNBRANCH) {
+  if (run->line_mode != MC_LINE_SCATTER) {
     if (!atomic || !meta || !atomic->dbr_offset || !atomic->dbr_line || !atomic->dbr_cdf)
       return fail(nullptr, MC_ERR_INVALID_ARG, "downbranch mode needs ion/upper per line and the branching table");
   }
+  if (run->line_mode == MC_LINE_MACROATOM &&
+      (!atomic->ma_jump_p || !atomic->ma_jump_offset || !atomic->ma_jump_target || !atomic->ma_jump_cdf))
+    return fail(nullptr, MC_ERR_INVALID_ARG, "macro-atom mode needs the ma_jump_* tables");
   uint32_t I = 0, K = 0;
   uint64_t nnz = 0;
   if (atomic) {
@@ -212,11 +218,32 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
         if (e > b && atomic->dbr_cdf[e - 1] != 1.0)
           return fail(nullptr, MC_ERR_INVALID_ARG, "each branching row must end at cdf == 1");
       }
-      if (run->line_mode == MC_LINE_DOWNBRANCH) {
+      if (run->line_mode != MC_LINE_SCATTER) {
         for (uint32_t j = 0; j < L; ++j) {
           const uint64_t r = static_cast<uint64_t>(lines->ion[j]) * K + lines->upper[j];
           if (atomic->dbr_offset[r + 1] == atomic->dbr_offset[r])
             return fail(nullptr, MC_ERR_INVALID_ARG, "a line's upper level has an empty branching row");
+        }
+      }
+      if (run->line_mode == MC_LINE_MACROATOM) {
+        const uint32_t *jo = atomic->ma_jump_offset;
+        if (jo[0] != 0) return fail(nullptr, MC_ERR_INVALID_ARG, "ma_jump_offset[0] must be 0");
+        for (uint64_t r = 0; r < rows; ++r) {
+          const double pj = atomic->ma_jump_p[r];
+          if (!(pj >= 0.0 && pj < 1.0)) return fail(nullptr, MC_ERR_INVALID_ARG, "ma_jump_p must be in [0, 1)");
+          if (jo[r + 1] < jo[r]) return fail(nullptr, MC_ERR_INVALID_ARG, "ma_jump_offset must be non-decreasing");
+          if (pj > 0.0 && jo[r + 1] == jo[r])
+            return fail(nullptr, MC_ERR_INVALID_ARG, "a level that jumps needs jump targets");
+          for (uint32_t k = jo[r]; k < jo[r + 1]; ++k) {
+            const int32_t t = atomic->ma_jump_target[k];
+            if (t < 0 || static_cast<uint64_t>(t) >= rows ||
+                atomic->dbr_offset[t + 1] == atomic->dbr_offset[t])
+              return fail(nullptr, MC_ERR_INVALID_ARG, "a jump target must be a level with a branching row");
+            if (!(atomic->ma_jump_cdf[k] >= 0.0) || (k > jo[r] && atomic->ma_jump_cdf[k] < atomic->ma_jump_cdf[k - 1]))
+              return fail(nullptr, MC_ERR_INVALID_ARG, "ma_jump_cdf must be non-decreasing within a row");
+          }
+          if (jo[r + 1] > jo[r] && atomic->ma_jump_cdf[jo[r + 1] - 1] != 1.0)
+            return fail(nullptr, MC_ERR_INVALID_ARG, "each jump row must end at cdf == 1");
         }
       }
     }
@@ -279,7 +306,7 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
     if (ok && atomic->dbr_offset)
       ok = alloc_n(m, &m->dbr_offset, IK + 1) && alloc_n(m, &m->dbr_line, nnz) &&
            alloc_n(m, &m->dbr_cdf, nnz);
-    if (ok && atomic->dbr_offset && meta && run->line_mode == MC_LINE_DOWNBRANCH)
+    if (ok && atomic->dbr_offset && meta && run->line_mode != MC_LINE_SCATTER)
       ok = alloc_n(m, &m->dbr_rec, nnz) && alloc_n(m, &m->dbr_bucket, nnz) &&
            alloc_n(m, &m->row_info, L);
   }
@@ -377,6 +404,35 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
                            m->dbr_cdf, m->nu, m->line_row, m->dbr_rec, m->dbr_bucket,
                            m->row_info, m->stream));
       m->launches += 2;
+    }
+    std::vector<MaRow> ma_rows;
+    std::vector<MaJump> ma_jumps;
+    if (run->line_mode == MC_LINE_MACROATOM) {
+      // decision thresholds ceil(p 2^53): z = u 2^-53 < p exactly when u < thr
+      const auto thr53 = [](double v) {
+        return static_cast<unsigned long long>(std::ceil(v * 9007199254740992.0));
+      };
+      const uint64_t rows = static_cast<uint64_t>(I) * K;
+      const uint32_t nj = atomic->ma_jump_offset[rows];
+      ma_rows.resize(rows);
+      ma_jumps.resize(nj > 0 ? nj : 1);
+      for (uint64_t r = 0; r < rows; ++r) {
+        MaRow &mr = ma_rows[r];
+        mr.jump_thr = thr53(atomic->ma_jump_p[r]);
+        mr.jump_begin = atomic->ma_jump_offset[r];
+        mr.jump_len = atomic->ma_jump_offset[r + 1] - atomic->ma_jump_offset[r];
+        mr.dbr_begin = atomic->dbr_offset[r];
+        mr.dbr_len = atomic->dbr_offset[r + 1] - atomic->dbr_offset[r];
+      }
+      for (uint32_t k = 0; k < nj; ++k) {
+        ma_jumps[k].thr = thr53(atomic->ma_jump_cdf[k]);
+        ma_jumps[k].target = atomic->ma_jump_target[k];
+        ma_jumps[k].pad = 0u;
+      }
+      if (!alloc_n(m, &m->ma_row, ma_rows.size()) || !alloc_n(m, &m->ma_jump, ma_jumps.size()))
+        return bail(MC_ERR_OOM, "device allocation failed");
+      chk(upload(m, m->ma_row, ma_rows.data(), ma_rows.size()));
+      chk(upload(m, m->ma_jump, ma_jumps.data(), ma_jumps.size()));
     }
     // Host buffers of the staged copies must outlive the async copies.
     chk(cudaStreamSynchronize(m->stream));
@@ -540,6 +596,8 @@ void model_fill_transport(const mc_model *m, TransportParams &p, uint64_t seed, 
   p.nu = m->nu; p.tau = m->tau; p.tau32 = m->tau32;
   p.line_row = m->line_row; p.dbr_offset = m->dbr_offset; p.dbr_line = m->dbr_line; p.dbr_cdf = m->dbr_cdf;
   p.j_est = m->j_est; p.nu_bar = m->nu_bar; p.j_blue = m->j_blue; p.spectrum = m->spectrum;
+  p.ma_row = m->ma_row;
+  p.ma_jump = m->ma_jump;
   p.n_virtual = static_cast<int32_t>(m->n_virtual);
   p.tau_v_max = m->tau_v_max;
   p.spectrum_v = m->n_virtual ? m->spectrum_v : nullptr;

@@ -47,6 +47,11 @@ struct DrawStream {
   static __device__ __forceinline__ uint64_t u53_of(uint32_t wa, uint32_t wb) {
     return (static_cast<uint64_t>(wa >> 5) << 26) | static_cast<uint64_t>(wb >> 6);
   }
+  // Draw d computed on its own (no cached half-block), d unchanged.
+  __device__ __forceinline__ uint64_t u53_at(uint32_t i) const {
+    const uint4 o = philox4x32_10(make_uint4(i >> 1, packet, iteration, 0u), k0, k1);
+    return (i & 1u) ? u53_of(o.z, o.w) : u53_of(o.x, o.y);
+  }
   // z in (0, 1]
   __device__ __forceinline__ double open0() { return __ull2double_rn(next_u53() + 1ull) * 0x1.0p-53; }
   // z in [0, 1)
@@ -221,11 +226,21 @@ struct WarpDraws {
     pid = pk;
   }
   // The live lane's next draw (u53, or the -ln z of an open-interval draw).
+  // A segment may take more draws than the buffer holds (a macro atom's
+  // internal jumps); past its end a draw is computed on its own.
   __device__ __forceinline__ unsigned long long next_u53(DrawStream &ds) const {
-    return on ? u[ds.d++ - base] : ds.next_u53();
+    if (!on) return ds.next_u53();
+    const uint32_t i = ds.d - base;
+    const unsigned long long v = i < kWarpDraws ? u[i] : ds.u53_at(ds.d);
+    ++ds.d;
+    return v;
   }
   __device__ __forceinline__ double next_tau(DrawStream &ds) const {
-    return on ? t[ds.d++ - base] : neg_log_u53(ds.next_u53() + 1ull);
+    if (!on) return neg_log_u53(ds.next_u53() + 1ull);
+    const uint32_t i = ds.d - base;
+    const double v = i < kWarpDraws ? t[i] : neg_log_u53(ds.u53_at(ds.d) + 1ull);
+    ++ds.d;
+    return v;
   }
 };
 

@@ -41,6 +41,22 @@ struct DbrRec {
   uint32_t guide;
 };
 
+// Macro-atom level (mode MC_LINE_MACROATOM), one per downbranch row: jump
+// when the decision draw u53 < jump_thr (= ceil(p 2^53), so exactly z < p),
+// target from the row's jump entries (first with u53 < thr), deactivation
+// through the downbranch row (begin, length).
+struct MaRow {
+  unsigned long long jump_thr;
+  uint32_t jump_begin, jump_len;
+  uint32_t dbr_begin, dbr_len;
+};
+struct MaJump {
+  unsigned long long thr;  // ceil(cdf 2^53)
+  int32_t target;          // row jumped to
+  uint32_t pad;
+};
+constexpr uint32_t kMaMaxJumps = 1024;
+
 // Everything the transport kernel reads or writes.
 struct TransportParams {
   int32_t S, L;
@@ -58,6 +74,8 @@ struct TransportParams {
   const double *inv_kappa;           // [S] 1/kappa (0 where kappa = 0), or nullptr
   const unsigned long long *row_info;// [L] row begin | row length << 32, or nullptr
   const DbrRec *dbr_rec;             // [nnz] guide-table rows, or nullptr
+  const MaRow *ma_row;               // [rows] macro-atom levels, or nullptr (no internal jumps)
+  const MaJump *ma_jump;             // [n] macro-atom jump entries
   const DbrRec *dbr_bucket;          // [nnz] bucket k of a row: copy of its guide entry's
                                      // record, guide field = that entry's position
   double *j_est, *nu_bar;            // [S] raw sums

@@ -36,6 +36,8 @@ struct mc_model {
   float *shell32 = nullptr;  // [4 S] binary32 x_in^2, x_out^2, kappa', 1/kappa' (mixed precision)
   unsigned long long *est_fix = nullptr;  // [2 S] fixed-point J, nu_bar sums (mixed precision)
   mcgpu::DbrRec *dbr_rec = nullptr, *dbr_bucket = nullptr;
+  mcgpu::MaRow *ma_row = nullptr;    // macro-atom levels (MC_LINE_MACROATOM)
+  mcgpu::MaJump *ma_jump = nullptr;
   unsigned long long *row_info = nullptr;
   float *kappa32 = nullptr, *x_in32 = nullptr, *x_out32 = nullptr;
   double *nu = nullptr, *tau = nullptr;

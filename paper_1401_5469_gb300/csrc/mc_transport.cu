@@ -110,6 +110,35 @@ __device__ __forceinline__ Emission downbranch_pick(const TransportParams &p, in
   return em;
 }
 
+// Macro atom (Sect. 2.5, mode macroatom): activated in level `row` (the
+// absorbing line's upper level), the atom jumps -- decision draw u53 below
+// the level's threshold, then a draw for the target -- until it deactivates;
+// returns the branching-row info (begin | length << 32) of the level it
+// deactivates from, for the emission pick.  After kMaMaxJumps jumps it
+// deactivates without the decision draw.
+__device__ __forceinline__ unsigned long long macroatom_walk(const TransportParams &p, int32_t row,
+                                                             const WarpDraws &wd, DrawStream &ds) {
+  for (uint32_t n = 0; n < kMaMaxJumps; ++n) {
+    const MaRow *mr = p.ma_row + row;
+    const unsigned long long thr = __ldg(&mr->jump_thr);
+    const uint2 jb = __ldg(reinterpret_cast<const uint2 *>(&mr->jump_begin));  // begin, length
+    const unsigned long long za = wd.next_u53(ds);
+    if (!(za < thr)) {
+      const uint2 db = __ldg(reinterpret_cast<const uint2 *>(&mr->dbr_begin));
+      return static_cast<unsigned long long>(db.x) | (static_cast<unsigned long long>(db.y) << 32);
+    }
+    const unsigned long long zb = wd.next_u53(ds);
+    const MaJump *jp = p.ma_jump + jb.x;
+    int32_t next = __ldg(&jp[jb.y - 1].target);
+    for (uint32_t k = 0; k < jb.y; ++k) {
+      if (zb < __ldg(&jp[k].thr)) { next = __ldg(&jp[k].target); break; }
+    }
+    row = next;
+  }
+  const uint2 db = __ldg(reinterpret_cast<const uint2 *>(&p.ma_row[row].dbr_begin));
+  return static_cast<unsigned long long>(db.x) | (static_cast<unsigned long long>(db.y) << 32);
+}
+
 // max(v, 0) through the integer keys (no binary64 instruction).
 __device__ __forceinline__ double max0(double v) { return rawkey(v) > 0 ? v : 0.0; }
 
@@ -475,7 +504,9 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         if (kind == kLineEvent) {
           pk.cnt[3] += 1u;
           if (MODE == 1) {
-            const Emission em = downbranch_pick(p, j, rinfo_hit, wd.next_u53(ds));
+            const unsigned long long rinfo_em =
+                p.ma_row ? macroatom_walk(p, __ldg(p.line_row + j), wd, ds) : rinfo_hit;
+            const Emission em = downbranch_pick(p, j, rinfo_em, wd.next_u53(ds));
             nu_c = em.nu;
             inv_nu_c = em.inv_nu;
             pk.next_line = em.line + 1;

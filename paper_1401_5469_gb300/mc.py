@@ -28,6 +28,7 @@ MC_ERR_UNSUPPORTED = -6
 MC_WARN_CAPPED = 1
 MC_LINE_SCATTER, MC_LINE_DOWNBRANCH = 0, 1
 MC_PRECISION_FP64, MC_PRECISION_MIXED = 0, 1
+MC_LINE_SCATTER, MC_LINE_DOWNBRANCH, MC_LINE_MACROATOM = 0, 1, 2
 MC_PACKET_ESCAPED, MC_PACKET_REABSORBED, MC_PACKET_CAPPED = 1, 2, 3
 MC_N_COUNTERS = 6
 COUNTER_NAMES = ("segments", "line_checks", "resonances", "line_interactions", "e_scatters",
@@ -61,7 +62,9 @@ class mc_atomic_desc(C.Structure):
     _fields_ = [("n_ions", C.c_uint32), ("n_levels", C.c_uint32), ("energy_ev", C.c_void_p),
                 ("g", C.c_void_p), ("metastable", C.c_void_p), ("n_ion", C.c_void_p),
                 ("dbr_offset", C.c_void_p), ("dbr_line", C.c_void_p), ("dbr_cdf", C.c_void_p),
-                ("lte_excitation", C.c_int32)]
+                ("lte_excitation", C.c_int32),
+                ("ma_jump_p", C.c_void_p), ("ma_jump_offset", C.c_void_p), ("ma_jump_target", C.c_void_p),
+                ("ma_jump_cdf", C.c_void_p)]
 
 
 class mc_run_desc(C.Structure):
@@ -371,10 +374,17 @@ class Model:
             nion = _f64(spec.n_ion)
             off, dl, cdf = _u32(spec.dbr_offset), _u32(spec.dbr_line), _f64(spec.dbr_cdf)
             k += [e, g, meta, nion, off, dl, cdf]
+            jp = jo = jt = jc = None
+            if getattr(spec, "ma_jump_p", None) is not None:
+                jp, jo = _f64(spec.ma_jump_p), _u32(spec.ma_jump_offset)
+                jt, jc = _i32(spec.ma_jump_target), _f64(spec.ma_jump_cdf)
+                k += [jp, jo, jt, jc]
             self.atomic = mc_atomic_desc(n_ions=int(spec.n_ions), n_levels=int(spec.n_levels),
                                          energy_ev=_p(e), g=_p(g), metastable=_p(meta),
                                          n_ion=_p(nion), dbr_offset=_p(off), dbr_line=_p(dl),
-                                         dbr_cdf=_p(cdf), lte_excitation=0)
+                                         dbr_cdf=_p(cdf), lte_excitation=0,
+                                         ma_jump_p=_p(jp), ma_jump_offset=_p(jo),
+                                         ma_jump_target=_p(jt), ma_jump_cdf=_p(jc))
         jb = spec.j_blue if j_blue is None else j_blue
         mp = int(max_packets if max_packets is not None else spec.n_packets)
         self.run = mc_run_desc(line_mode=int(spec.line_mode), precision=int(precision),
