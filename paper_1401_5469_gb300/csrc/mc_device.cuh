@@ -47,11 +47,6 @@ struct DrawStream {
   static __device__ __forceinline__ uint64_t u53_of(uint32_t wa, uint32_t wb) {
     return (static_cast<uint64_t>(wa >> 5) << 26) | static_cast<uint64_t>(wb >> 6);
   }
-  // Draw d computed on its own (no cached half-block), d unchanged.
-  __device__ __forceinline__ uint64_t u53_at(uint32_t i) const {
-    const uint4 o = philox4x32_10(make_uint4(i >> 1, packet, iteration, 0u), k0, k1);
-    return (i & 1u) ? u53_of(o.z, o.w) : u53_of(o.x, o.y);
-  }
   // z in (0, 1]
   __device__ __forceinline__ double open0() { return __ull2double_rn(next_u53() + 1ull) * 0x1.0p-53; }
   // z in [0, 1)
@@ -186,6 +181,19 @@ __device__ __forceinline__ double neg_log_u53(unsigned long long u) {
 constexpr uint32_t kWarpDraws = 64;
 constexpr uint32_t kNoPacket = 0xffffffffu;
 
+// Draw i of a packet's stream computed on its own, for draws past the end of
+// the warp buffer (only a macro atom's long walks get there).  Out of line
+// and by value, so that the common path does not evaluate it.
+static __device__ __noinline__ unsigned long long u53_past_buffer(uint32_t k0, uint32_t k1, uint32_t packet,
+                                                           uint32_t iteration, uint32_t i) {
+  const uint4 o = philox4x32_10(make_uint4(i >> 1, packet, iteration, 0u), k0, k1);
+  return (i & 1u) ? DrawStream::u53_of(o.z, o.w) : DrawStream::u53_of(o.x, o.y);
+}
+static __device__ __noinline__ double tau_past_buffer(uint32_t k0, uint32_t k1, uint32_t packet, uint32_t iteration,
+                                               uint32_t i) {
+  return neg_log_u53(u53_past_buffer(k0, k1, packet, iteration, i) + 1ull);
+}
+
 struct WarpDraws {
   unsigned long long *u;  // [64] u53 of draws base .. base + 63 (shared memory, per warp)
   double *t;              // [64] -ln((u53 + 1) 2^-53) of the same draws
@@ -226,21 +234,23 @@ struct WarpDraws {
     pid = pk;
   }
   // The live lane's next draw (u53, or the -ln z of an open-interval draw).
-  // A segment may take more draws than the buffer holds (a macro atom's
-  // internal jumps); past its end a draw is computed on its own.
+  // UNBOUNDED: a segment may take more draws than the buffer holds (a macro
+  // atom's internal jumps), and past its end a draw is computed on its own;
+  // otherwise a segment takes at most three draws and prepare() keeps three
+  // in the buffer.
+  template <bool UNBOUNDED>
   __device__ __forceinline__ unsigned long long next_u53(DrawStream &ds) const {
     if (!on) return ds.next_u53();
-    const uint32_t i = ds.d - base;
-    const unsigned long long v = i < kWarpDraws ? u[i] : ds.u53_at(ds.d);
-    ++ds.d;
-    return v;
+    const uint32_t i = ds.d++ - base;
+    if (!UNBOUNDED || i < kWarpDraws) return u[i];
+    return u53_past_buffer(ds.k0, ds.k1, ds.packet, ds.iteration, ds.d - 1u);
   }
+  template <bool UNBOUNDED>
   __device__ __forceinline__ double next_tau(DrawStream &ds) const {
     if (!on) return neg_log_u53(ds.next_u53() + 1ull);
-    const uint32_t i = ds.d - base;
-    const double v = i < kWarpDraws ? t[i] : neg_log_u53(ds.u53_at(ds.d) + 1ull);
-    ++ds.d;
-    return v;
+    const uint32_t i = ds.d++ - base;
+    if (!UNBOUNDED || i < kWarpDraws) return t[i];
+    return tau_past_buffer(ds.k0, ds.k1, ds.packet, ds.iteration, ds.d - 1u);
   }
 };
 

@@ -122,12 +122,12 @@ __device__ __forceinline__ unsigned long long macroatom_walk(const TransportPara
     const MaRow *mr = p.ma_row + row;
     const unsigned long long thr = __ldg(&mr->jump_thr);
     const uint2 jb = __ldg(reinterpret_cast<const uint2 *>(&mr->jump_begin));  // begin, length
-    const unsigned long long za = wd.next_u53(ds);
+    const unsigned long long za = wd.template next_u53<true>(ds);
     if (!(za < thr)) {
       const uint2 db = __ldg(reinterpret_cast<const uint2 *>(&mr->dbr_begin));
       return static_cast<unsigned long long>(db.x) | (static_cast<unsigned long long>(db.y) << 32);
     }
-    const unsigned long long zb = wd.next_u53(ds);
+    const unsigned long long zb = wd.template next_u53<true>(ds);
     const MaJump *jp = p.ma_jump + jb.x;
     int32_t next = __ldg(&jp[jb.y - 1].target);
     for (uint32_t k = 0; k < jb.y; ++k) {
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       const double kap = s_kap[s];
       const bool thomson = kap > 0.0;
       // optical depth to the next event, tau = -ln z
-      double tau_rem = wd.next_tau(ds);
+      double tau_rem = wd.template next_tau<MODE == 2>(ds);
       // Shell boundary: at the exit point x mu = p_exit = +-sqrt(x_b^2 - q) (the
       // inner sphere is hit when moving inward with q <= x_in^2), so the path
       // length is p_exit - p and the comoving frequency there nu_lab (1 - p_exit).
@@ -401,12 +401,12 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       if (j < L) {
         bj = __ldg(nub + j);
         taul = __ldg(tau_s + j);
-        if (MODE == 1 && p.row_info) rinfo = __ldg(p.row_info + j);
+        if (MODE >= 1 && p.row_info) rinfo = __ldg(p.row_info + j);
       }
       if (j + 1 < L) {
         bj_n = __ldg(nub + j + 1);
         tau_n = __ldg(tau_s + j + 1);
-        if (MODE == 1 && p.row_info) rinfo_n = __ldg(p.row_info + j + 1);
+        if (MODE >= 1 && p.row_info) rinfo_n = __ldg(p.row_info + j + 1);
       }
       while (j < L) {
         pk.cnt[1] += 1u;
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         if (j + 2 < L) {
           bj_nn = __ldg(nub + j + 2);
           tau_nn = __ldg(tau_s + j + 2);
-          if (MODE == 1 && p.row_info) rinfo_nn = __ldg(p.row_info + j + 2);
+          if (MODE >= 1 && p.row_info) rinfo_nn = __ldg(p.row_info + j + 2);
         }
         if (bj <= key_thr) break;  // the Sobolev point lies beyond d_e (or the shell exit)
         const double nuj = __longlong_as_double(bj);
@@ -503,10 +503,11 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         double nu_c, inv_nu_c;
         if (kind == kLineEvent) {
           pk.cnt[3] += 1u;
-          if (MODE == 1) {
+          if (MODE >= 1) {
+            // MODE 2: macro atom, internal jumps before the emission pick
             const unsigned long long rinfo_em =
-                p.ma_row ? macroatom_walk(p, __ldg(p.line_row + j), wd, ds) : rinfo_hit;
-            const Emission em = downbranch_pick(p, j, rinfo_em, wd.next_u53(ds));
+                MODE == 2 ? macroatom_walk(p, __ldg(p.line_row + j), wd, ds) : rinfo_hit;
+            const Emission em = downbranch_pick(p, j, rinfo_em, wd.template next_u53<MODE == 2>(ds));
             nu_c = em.nu;
             inv_nu_c = em.inv_nu;
             pk.next_line = em.line + 1;
@@ -521,7 +522,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
           inv_nu_c = inv_nu * rcp64(D1);
         }
         // isotropic re-emission: new direction, lab values from the comoving ones
-        const double mu2 = DrawStream::mu_from_u53(wd.next_u53(ds));
+        const double mu2 = DrawStream::mu_from_u53(wd.template next_u53<MODE == 2>(ds));
         const double pn = xn * mu2;
         const double D2 = 1.0 - pn;
         const double iD2 = rcp64(D2);
@@ -585,6 +586,10 @@ const void *select_kernel(int line_mode, int precision, bool jb, bool rec) {
   if (line_mode == 0) {
     if (jb) return rec ? kernel_ptr<0, true, true>() : kernel_ptr<0, true, false>();
     return rec ? kernel_ptr<0, false, true>() : kernel_ptr<0, false, false>();
+  }
+  if (line_mode == 2) {
+    if (jb) return rec ? kernel_ptr<2, true, true>() : kernel_ptr<2, true, false>();
+    return rec ? kernel_ptr<2, false, true>() : kernel_ptr<2, false, false>();
   }
   if (jb) return rec ? kernel_ptr<1, true, true>() : kernel_ptr<1, true, false>();
   return rec ? kernel_ptr<1, false, true>() : kernel_ptr<1, false, false>();
