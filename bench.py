@@ -424,8 +424,9 @@ def run_batched(args):
     stream = torch.cuda.current_stream()
 
     # ---- batched, mixed precision
+    jb = bool(args.j_blue)
     t0 = time.perf_counter()
-    models = [mc.Model(s, precision=mc.MC_PRECISION_MIXED) for s in specs]
+    models = [mc.Model(s, precision=mc.MC_PRECISION_MIXED, j_blue=jb) for s in specs]
     for m in models:
         m.set_plasma()
     b = mc.Batch(models)
@@ -471,7 +472,7 @@ def run_batched(args):
     t_fp64 = []
 
     def fp64_loop(spec, seed):
-        m = mc.Model(spec)
+        m = mc.Model(spec, j_blue=jb)
         m.set_plasma()
         for it in range(n_it):
             m.run_iteration(seed, it, spec.n_packets, spec.t_inner)
@@ -503,7 +504,7 @@ def run_batched(args):
                    "models": n_models, "iterations": n_it, "packets_per_iteration": total_packets,
                    "shells": [min(s.n_shells for s in specs), max(s.n_shells for s in specs)],
                    "lines": [min(s.n_lines for s in specs), max(s.n_lines for s in specs)],
-                   "j_blue": bool(specs[0].j_blue), "line_mode": "downbranch",
+                   "j_blue": jb, "line_mode": "downbranch",
                    "l2": "inputs larger than L2 (Sobolev depths and J_blue of all models)"},
         "packets_per_s": total_packets * n_it / batched_s,
         "segments_per_s": work["segments"] / (1e-3 * sum(transport_ms)),
@@ -732,6 +733,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--tick-packets", type=int, default=0)
+    ap.add_argument("--j-blue", type=int, default=1, choices=[0, 1], help="J_blue estimators (batched workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -248,6 +248,23 @@ mc_status mc_read_transport_phases(mc_model *m, float *ms);
 /* Number of kernels this model has launched since creation. */
 mc_status mc_launch_count(const mc_model *m, uint64_t *count);
 
+/* Inner-boundary temperature (Sect. 2.8).  Eq. 18: *t_inner such that
+ * 4 pi r_inner^2 sigma_SB t_inner^4 = l_outer (erg/s), r_inner = v_inner[0]
+ * t_exp of the model.  Errors: MC_ERR_INVALID_ARG (NULL, l_outer <= 0). */
+mc_status mc_t_inner_from_luminosity(const mc_model *m, double l_outer, double *t_inner);
+
+/* Luminosity emitted in the last iteration: the lab-frame energy of the
+ * escaping packets (every spectrum bin, including the two outside the
+ * range, summed in bin order) divided by delta_t, in erg/s.  Synchronises
+ * the model's stream.  Errors: MC_ERR_INVALID_ARG, MC_ERR_NOT_READY. */
+mc_status mc_emitted_luminosity(mc_model *m, double *l_emitted);
+
+/* T_inner for the next iteration so that the emitted luminosity would match
+ * the requested one if it scaled like T_inner^4 (the paper raises T_inner
+ * when too little escapes and lowers it otherwise):
+ * t_inner (l_requested / l_emitted)^(1/4); t_inner when l_emitted <= 0. */
+double mc_t_inner_update(double t_inner, double l_requested, double l_emitted);
+
 /* Virtual packets (Sect. 2.9, Eqs. 19-21) in the following iterations: at
  * injection and after every interaction each packet spawns n_virtual
  * v-packets with directions uniform in (mu_min, 1], mu_min = -sqrt(1 -

@@ -128,6 +128,12 @@ def lib():
             L.orc_run_traced.restype = i32
             L.orc_run_traced.argtypes = [C.POINTER(_Model), u64, u32, u64, d, u64, u64,
                                          C.POINTER(_Result), C.POINTER(_Trace)]
+            L.orc_t_inner_from_luminosity.restype = d
+            L.orc_t_inner_from_luminosity.argtypes = [d, d]
+            L.orc_emitted_luminosity.restype = d
+            L.orc_emitted_luminosity.argtypes = [vp, i32, d]
+            L.orc_t_inner_update.restype = d
+            L.orc_t_inner_update.argtypes = [d, d, d]
             L.orc_macroatom_walks.argtypes = [C.POINTER(_Model), i32, u64, i64, vp, vp]
             L.orc_virtual_tau.restype = d
             L.orc_virtual_tau.argtypes = [C.POINTER(_Model), d, d, i32, d, i32]
@@ -415,6 +421,22 @@ def update_radiation_field(spec, j_raw, nu_bar_raw, t_rad, w, delta_t=1.0):
     t, ww = _f64(t_rad).copy(), _f64(w).copy()
     lib().orc_update_radiation_field(S, _p(_f64(j_raw)), _p(_f64(nu_bar_raw)), _p(norm), _p(t), _p(ww))
     return t, ww
+
+
+def t_inner_from_luminosity(spec, l_outer):
+    """Eq. 18: T_inner with 4 pi r_i^2 sigma T_inner^4 = L_outer."""
+    return float(lib().orc_t_inner_from_luminosity(float(spec.v_inner[0] * spec.t_exp), float(l_outer)))
+
+
+def emitted_luminosity(spectrum, delta_t=1.0):
+    """Lab-frame energy of the escaping packets per unit time (all bins)."""
+    sp = _f64(spectrum)
+    return float(lib().orc_emitted_luminosity(_p(sp), sp.size, float(delta_t)))
+
+
+def t_inner_update(t_inner, l_requested, l_emitted):
+    """T_inner (L_requested / L_emitted)^(1/4); unchanged if nothing escaped."""
+    return float(lib().orc_t_inner_update(float(t_inner), float(l_requested), float(l_emitted)))
 
 
 def plasma_tau(spec, t_rad, w):

@@ -998,3 +998,31 @@ void orc_update_radiation_field(int32_t S, const double *j_raw, const double *nu
 }
 
 int32_t orc_abi_version(void) { return 1; }
+
+/* ------------------------------------------------------------ inner boundary
+ * Sect. 2.8.  Eq. 18: first guess of T_inner from the requested luminosity
+ * at the outer boundary, L_o = 4 pi r_i^2 sigma T_i^4.  The emitted
+ * luminosity is the lab-frame energy of the escaping packets per unit time
+ * (every bin of the spectrum, including the two outside the range).  After an
+ * iteration T_inner moves so that the emitted luminosity would match the
+ * requested one if it scaled like T_inner^4: T <- T (L_o / L_emitted)^(1/4);
+ * with no escaping energy T_inner is kept.
+ */
+double orc_t_inner_from_luminosity(double r_inner, double l_outer)
+{
+    double x = l_outer / ((((4.0 * PI_D) * r_inner) * r_inner) * SIGMA_SB);
+    return sqrt(sqrt(x));
+}
+
+double orc_emitted_luminosity(const double *spectrum, int32_t n_bins_total, double delta_t)
+{
+    double s = 0.0;
+    for (int32_t b = 0; b < n_bins_total; ++b) s += spectrum[b];
+    return s / delta_t;
+}
+
+double orc_t_inner_update(double t_inner, double l_requested, double l_emitted)
+{
+    if (!(l_emitted > 0.0)) return t_inner;
+    return t_inner * sqrt(sqrt(l_requested / l_emitted));
+}

@@ -721,6 +721,32 @@ mc_status mc_read_spectrum(mc_model *m, double *spectrum, mc_packet_stats *stats
   return c[kStCapped] ? MC_WARN_CAPPED : MC_OK;
 }
 
+mc_status mc_t_inner_from_luminosity(const mc_model *m, double l_outer, double *t_inner) {
+  if (!m || !t_inner || !(l_outer > 0.0) || !std::isfinite(l_outer)) return MC_ERR_INVALID_ARG;
+  const double r_i = m->r_inner;
+  *t_inner = std::sqrt(std::sqrt(l_outer / ((((4.0 * kPi) * r_i) * r_i) * kSigmaSB)));
+  return MC_OK;
+}
+
+mc_status mc_emitted_luminosity(mc_model *m, double *l_emitted) {
+  if (!m || !l_emitted) return MC_ERR_INVALID_ARG;
+  if (!m->have_run) return fail(m, MC_ERR_NOT_READY, "no run yet");
+  std::vector<double> sp(static_cast<size_t>(m->run.spec_bins) + 2);
+  cudaError_t e = cudaMemcpyAsync(sp.data(), m->spectrum, sp.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                  m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(m, e, "read spectrum");
+  double s = 0.0;
+  for (double v : sp) s += v;
+  *l_emitted = s / m->run.delta_t;
+  return MC_OK;
+}
+
+double mc_t_inner_update(double t_inner, double l_requested, double l_emitted) {
+  if (!(l_emitted > 0.0)) return t_inner;
+  return t_inner * std::sqrt(std::sqrt(l_requested / l_emitted));
+}
+
 mc_status mc_set_virtual_packets(mc_model *m, uint32_t n_virtual, double tau_v_max) {
   if (!m) return MC_ERR_INVALID_ARG;
   if (m->run.precision != MC_PRECISION_FP64)

@@ -43,7 +43,8 @@ EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_run_iter
             "mc_batch_create", "mc_batch_run_iteration", "mc_batch_synchronize",
             "mc_batch_read_timing", "mc_batch_last_error_message", "mc_batch_destroy",
             "mc_batch_set_launch", "mc_batch_get_launch", "mc_batch_autotune",
-            "mc_device_estimators", "mc_set_virtual_packets", "mc_read_virtual_spectrum")
+            "mc_device_estimators", "mc_set_virtual_packets", "mc_read_virtual_spectrum",
+            "mc_t_inner_from_luminosity", "mc_emitted_luminosity", "mc_t_inner_update")
 
 MC_ORDER_PACKETS, MC_ORDER_WORK, MC_ORDER_GIVEN = 0, 1, 2
 
@@ -195,6 +196,12 @@ def load(build_if_missing: bool = True):
     L.mc_batch_last_error_message.argtypes = [vp]
     L.mc_batch_destroy.restype = None
     L.mc_batch_destroy.argtypes = [vp]
+    L.mc_t_inner_from_luminosity.restype = i32
+    L.mc_t_inner_from_luminosity.argtypes = [vp, d, P(d)]
+    L.mc_emitted_luminosity.restype = i32
+    L.mc_emitted_luminosity.argtypes = [vp, P(d)]
+    L.mc_t_inner_update.restype = d
+    L.mc_t_inner_update.argtypes = [d, d, d]
     L.mc_set_virtual_packets.restype = i32
     L.mc_set_virtual_packets.argtypes = [vp, u32, d]
     L.mc_read_virtual_spectrum.restype = i32
@@ -435,6 +442,18 @@ class Model:
         mc_read_estimators(self.h, j, nb, jb, norm)
         return j, nb, jb, norm
 
+    def t_inner_from_luminosity(self, l_outer: float) -> float:
+        """Eq. 18: T_inner whose inner-boundary luminosity is l_outer."""
+        t = C.c_double()
+        _check(load().mc_t_inner_from_luminosity(self.h, float(l_outer), C.byref(t)), self.h)
+        return t.value
+
+    def emitted_luminosity(self) -> float:
+        """Lab-frame energy of the last iteration's escaping packets per unit time."""
+        v = C.c_double()
+        _check(load().mc_emitted_luminosity(self.h, C.byref(v)), self.h)
+        return v.value
+
     def set_virtual_packets(self, n_virtual: int, tau_v_max: float = 0.0):
         """Virtual packets (Sect. 2.9) in the following iterations (0: off)."""
         return _check(load().mc_set_virtual_packets(self.h, int(n_virtual), float(tau_v_max)), self.h)
@@ -490,6 +509,11 @@ class Model:
 
     def synchronize(self):
         return mc_synchronize(self.h)
+
+
+def t_inner_update(t_inner: float, l_requested: float, l_emitted: float) -> float:
+    """mc_t_inner_update: T_inner (l_requested / l_emitted)^(1/4)."""
+    return float(load().mc_t_inner_update(float(t_inner), float(l_requested), float(l_emitted)))
 
 
 # ----------------------------------------------------------------- batches

@@ -90,3 +90,9 @@ def test_batch_calls_reject_null_arguments():
     h = C.c_void_p()
     assert L.mc_batch_create(None, 0, C.byref(h)) == mc.MC_ERR_INVALID_ARG
     assert not h.value
+
+
+def test_t_inner_update_matches_the_oracle():
+    import oracle
+    for t, lr, le in ((9000.0, 4e42, 3.1e42), (12000.0, 1e41, 2e41), (8000.0, 1e42, 0.0)):
+        assert mc.t_inner_update(t, lr, le) == oracle.t_inner_update(t, lr, le)

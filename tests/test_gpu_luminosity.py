@@ -1,0 +1,51 @@
+"""Inner-boundary temperature cycle on the GPU (Sect. 2.8, Eq. 18).
+
+* mc_t_inner_from_luminosity equals the oracle's Eq. 18;
+* the emitted luminosity of the scatter model's iteration equals the
+  oracle's (1e-9: the spectrum bins differ only in summation order);
+* transparent ejecta: one update of T_inner reproduces the requested
+  luminosity to rounding (with the same draws the emitted luminosity scales
+  exactly as T_inner^4).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_5469_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1401_5469_gb300 import mc as mcmod
+    mcmod.load()
+    return mcmod
+
+
+def test_eq18_and_emitted_luminosity_match_the_oracle(mc):
+    spec = synth.scatter_model()
+    m = mc.Model(spec)
+    assert m.t_inner_from_luminosity(3e42) == pytest.approx(oracle.t_inner_from_luminosity(spec, 3e42), rel=1e-15)
+    m.set_plasma(tau=spec.tau)
+    m.run_iteration(5469, 0, spec.n_packets, spec.t_inner)
+    l_gpu = m.emitted_luminosity()
+    m.close()
+    om = oracle.OracleModel(spec, tau=spec.tau)
+    r = oracle.run_iteration(om, 5469, 0, spec.n_packets, spec.t_inner, threads=8, record=False)
+    assert l_gpu == pytest.approx(oracle.emitted_luminosity(r.spectrum), rel=1e-9)
+
+
+def test_one_update_reaches_the_requested_luminosity(mc):
+    spec = synth.free_streaming_model(n_packets=20000)
+    m = mc.Model(spec)
+    m.set_plasma(tau=spec.tau)
+    l_req, t0 = 4.0e42, 9000.0
+    m.run_iteration(5, 0, spec.n_packets, t0)
+    t1 = mc.t_inner_update(t0, l_req, m.emitted_luminosity())
+    m.run_iteration(5, 0, spec.n_packets, t1)
+    assert m.emitted_luminosity() == pytest.approx(l_req, rel=1e-12)
+    m.close()

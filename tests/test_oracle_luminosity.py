@@ -1,0 +1,56 @@
+"""Pins of the inner-boundary temperature cycle (Sect. 2.8, Eq. 18).
+
+* Eq. 18 inverts L = 4 pi r_i^2 sigma T^4;
+* transparent ejecta: every packet escapes with lab energy E / D, so the
+  emitted luminosity is N E <1/D> / dt, whose expectation is
+  L_i int_0^1 2 mu / (1 - mu x) dmu (closed form);
+* with the same draws, a transparent model's emitted luminosity scales
+  exactly as T_inner^4 (packet energies scale so, directions do not depend
+  on T), so one update T <- T (L_o / L_em)^(1/4) reproduces L_o to rounding;
+* nothing escaping leaves T_inner unchanged.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_5469_gb300 import synth
+
+SIGMA_SB = 5.670374419e-5
+
+
+def test_eq18_inverts_the_inner_luminosity():
+    spec = synth.free_streaming_model()
+    r_i = spec.v_inner[0] * spec.t_exp
+    for lum in (1e40, 3.2e42, 7e43):
+        t = oracle.t_inner_from_luminosity(spec, lum)
+        assert 4 * np.pi * r_i ** 2 * SIGMA_SB * t ** 4 == pytest.approx(lum, rel=1e-14)
+
+
+def test_free_streaming_emitted_luminosity():
+    spec = synth.free_streaming_model(n_packets=40000)
+    om = oracle.OracleModel(spec)
+    r = oracle.run_iteration(om, 17, 0, spec.n_packets, spec.t_inner, threads=4, record=True)
+    l_em = oracle.emitted_luminosity(r.spectrum)
+    assert l_em == pytest.approx(r.energy.sum(), rel=1e-12)  # every packet escapes
+    r_i = spec.v_inner[0] * spec.t_exp
+    l_i = 4 * np.pi * r_i ** 2 * SIGMA_SB * spec.t_inner ** 4
+    x = spec.v_inner[0] / 2.99792458e10
+    mean = -2.0 / x - 2.0 * np.log1p(-x) / x ** 2
+    e = r.energy / (l_i / spec.n_packets)  # 1/D per packet
+    assert abs(l_em / l_i - mean) < 5 * e.std(ddof=1) / np.sqrt(e.size)
+
+
+def test_one_update_reaches_the_requested_luminosity_in_free_streaming():
+    spec = synth.free_streaming_model(n_packets=5000)
+    om = oracle.OracleModel(spec)
+    l_req = 4.0e42
+    t0 = 9000.0
+    r0 = oracle.run_iteration(om, 5, 0, spec.n_packets, t0, threads=4, record=False)
+    t1 = oracle.t_inner_update(t0, l_req, oracle.emitted_luminosity(r0.spectrum))
+    r1 = oracle.run_iteration(om, 5, 0, spec.n_packets, t1, threads=4, record=False)
+    assert oracle.emitted_luminosity(r1.spectrum) == pytest.approx(l_req, rel=1e-12)
+    assert t1 != t0
+
+
+def test_nothing_escaping_keeps_t_inner():
+    assert oracle.t_inner_update(9000.0, 1e42, 0.0) == 9000.0
