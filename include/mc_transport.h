@@ -127,7 +127,7 @@ typedef struct {
 
 /* Run options. */
 typedef struct {
-    int32_t line_mode;          /* MC_LINE_* */
+    int32_t line_mode;          /* MC_LINE_* (MC_LINE_MACROATOM: binary64 only) */
     int32_t precision;          /* MC_PRECISION_* */
     int32_t j_blue;             /* 1: accumulate J_blue estimators (Eq. 17) */
     int32_t record_packets;     /* 1: keep per-packet fates for mc_read_packets */
@@ -427,7 +427,7 @@ typedef struct {
     uint32_t n_lines;
     const double *nu;                     /* [L] device, strictly descending */
     const double *tau;                    /* [S*L] device, shell-major Sobolev depths */
-    int32_t line_mode;                    /* MC_LINE_* */
+    int32_t line_mode;                    /* MC_LINE_SCATTER or MC_LINE_DOWNBRANCH */
     const int32_t *line_row;              /* [L] device: ion*n_levels + upper (downbranch) */
     const uint32_t *dbr_offset, *dbr_line;/* device branching table (downbranch) */
     const double *dbr_cdf;
