@@ -128,6 +128,8 @@ def lib():
             L.orc_run_traced.restype = i32
             L.orc_run_traced.argtypes = [C.POINTER(_Model), u64, u32, u64, d, u64, u64,
                                          C.POINTER(_Result), C.POINTER(_Trace)]
+            L.orc_ionization.restype = i32
+            L.orc_ionization.argtypes = [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, d, vp, vp, vp, i32, vp, vp]
             L.orc_t_inner_from_luminosity.restype = d
             L.orc_t_inner_from_luminosity.argtypes = [d, d]
             L.orc_emitted_luminosity.restype = d
@@ -252,6 +254,11 @@ class OracleModel:
         self.tau_v_max = float(tau_v_max)
         self._refresh()
 
+    def set_electron_density(self, n_e):
+        """Electron density per shell for the Thomson opacity (ionization modes)."""
+        self.n_e = _f64(n_e).copy()
+        self._refresh()
+
     def set_tau(self, tau):
         self.tau = _f64(tau).reshape(self.v_inner.size, self.nu.size)
         self._refresh()
@@ -370,12 +377,36 @@ def downbranch_pick(om: OracleModel, row: int, z: float) -> int:
 
 # ------------------------------------------------------------------ plasma / radiation field
 
-def level_populations(spec, t_rad, w, lte_excitation=False):
+def ion_of(spec):
+    """[E * J] ion index of each (element, stage), -1 for stages without levels."""
+    E, J = int(spec.n_elements), int(spec.n_stages)
+    out = np.full(E * J, -1, dtype=np.int32)
+    for a, (e, j) in enumerate(zip(spec.ion_element, spec.ion_stage)):
+        out[int(e) * J + int(j)] = a
+    return out
+
+
+def ionization_state(spec, t_rad, w):
+    """Ion densities [S, I] and electron density [S] from the ionization
+    balance of Sect. 2.3 (Eq. 2 or 3, charge conservation)."""
+    S, I, K = spec.n_shells, int(spec.n_ions), int(spec.n_levels)
+    E, J = int(spec.n_elements), int(spec.n_stages)
+    n_ion, n_e = np.zeros(S * I), np.zeros(S)
+    rc = lib().orc_ionization(S, I, K, E, J, _p(ion_of(spec)), _p(_f64(spec.energy_ev)), _p(_f64(spec.g)),
+                              _p(_f64(spec.chi_ev)), _p(_f64(spec.zeta)), float(spec.delta),
+                              _p(_f64(spec.n_element)), _p(_f64(t_rad)), _p(_f64(w)),
+                              int(spec.ionization_mode), _p(n_ion), _p(n_e))
+    if rc != 0:
+        raise ValueError("oracle rejected the ionization data")
+    return n_ion.reshape(S, I), n_e
+
+
+def level_populations(spec, t_rad, w, lte_excitation=False, n_ion=None):
     S, I, K = spec.n_shells, int(spec.n_ions), int(spec.n_levels)
     t_rad, w = _f64(t_rad), _f64(w)
     e, g = _f64(spec.energy_ev), _f64(spec.g)
     meta = np.ascontiguousarray(spec.metastable, dtype=np.uint8)
-    n_ion = _f64(spec.n_ion)
+    n_ion = _f64(spec.n_ion if n_ion is None else n_ion)
     n = np.zeros(S * I * K)
     lib().orc_level_populations(S, I, K, _p(t_rad), _p(w), _p(e), _p(g), _p(meta), _p(n_ion),
                                 int(bool(lte_excitation)), _p(n))
@@ -440,8 +471,10 @@ def t_inner_update(t_inner, l_requested, l_emitted):
 
 
 def plasma_tau(spec, t_rad, w):
-    """Sobolev depths from dilute-lte populations (Eqs. 5 and 12)."""
-    return sobolev_tau(spec, level_populations(spec, t_rad, w))
+    """Sobolev depths from dilute-lte populations (Eqs. 5 and 12); with an
+    ionization mode the ion densities come from the ionization balance."""
+    n_ion = ionization_state(spec, t_rad, w)[0] if getattr(spec, "ionization_mode", 0) else None
+    return sobolev_tau(spec, level_populations(spec, t_rad, w, n_ion=n_ion))
 
 
 def run_loop(spec, n_iterations, n_packets, seed, threads=1, t_inner=None, record=False,
@@ -455,14 +488,19 @@ def run_loop(spec, n_iterations, n_packets, seed, threads=1, t_inner=None, recor
     w = geometric_dilution(spec)
     om = None
     out = []
+    ionized = getattr(spec, "ionization_mode", 0) and spec.tau is None
     for it in range(n_iterations):
         tau = plasma_tau(spec, t_rad, w) if spec.tau is None else spec.tau
         if om is None:
             om = OracleModel(spec, tau=tau, max_segments=max_segments)
         else:
             om.set_tau(tau)
+        n_e = None
+        if ionized:  # the Thomson opacity follows the electron density
+            n_e = ionization_state(spec, t_rad, w)[1]
+            om.set_electron_density(n_e)
         r = run_iteration(om, seed, it, n_packets, t_in, threads=threads, record=record)
-        r.t_rad_in, r.w_in, r.tau = t_rad.copy(), w.copy(), tau
+        r.t_rad_in, r.w_in, r.tau, r.n_e = t_rad.copy(), w.copy(), tau, n_e
         t_rad, w = update_radiation_field(spec, r.j_est, r.nu_bar, t_rad, w)
         r.t_rad_out, r.w_out = t_rad.copy(), w.copy()
         out.append(r)

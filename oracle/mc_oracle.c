@@ -1026,3 +1026,96 @@ double orc_t_inner_update(double t_inner, double l_requested, double l_emitted)
     if (!(l_emitted > 0.0)) return t_inner;
     return t_inner * sqrt(sqrt(l_requested / l_emitted));
 }
+
+/* ------------------------------------------------------------ ionization
+ * Sect. 2.3.  Per shell, the ratio of successive ionization stages of an
+ * element, Phi'_{e,j} = N_{e,j+1} n_e / N_{e,j}, is the Saha-Boltzmann value
+ * (lte mode, Eq. 2)
+ *   Phi = 2 Z_{j+1}/Z_j (2 pi m_e k T_R / h^2)^(3/2) exp(-chi_j / k T_R)
+ * or the modified nebular value (nebular mode, Eq. 3)
+ *   Phi' = W [delta zeta_j + W (1 - zeta_j)] (T_e / T_R)^(1/2) Phi,  T_e = 0.9 T_R.
+ * Z_j is the LTE partition function sum_k g_k exp(-eps_k / k T_R) of a stage
+ * with levels, 1 for a stage without (ion_of[e*J + j] < 0).  For a trial n_e
+ * the stage fractions follow from the ratios; n_e itself is the root of
+ * charge conservation n_e = sum_e N_e sum_j j f_{e,j}(n_e) (the right side
+ * falls as n_e grows, so the root is unique), found by bisection on ln n_e
+ * with the geometric midpoint sqrt(lo hi).
+ * Outputs: n_ion[S*I] for the stages with levels, n_e[S].
+ */
+#define ORC_ION_MAX_STAGES 16
+static void stage_fractions(int32_t J, const double *phi, double n_e, double *f)
+{
+    double r = 1.0, sum = 1.0;
+    f[0] = 1.0;
+    for (int32_t j = 1; j < J; ++j) {
+        r = r * (phi[j - 1] / n_e);
+        f[j] = r;
+        sum += r;
+    }
+    for (int32_t j = 0; j < J; ++j) f[j] = f[j] / sum;
+}
+
+int orc_ionization(int32_t S, int32_t I, int32_t K, int32_t E, int32_t J, const int32_t *ion_of,
+                   const double *energy_ev, const double *g, const double *chi_ev, const double *zeta,
+                   double delta, const double *n_element, const double *t_rad, const double *w,
+                   int32_t mode, double *n_ion, double *n_e)
+{
+    if (J < 2 || J > ORC_ION_MAX_STAGES || (mode != 1 && mode != 2)) return -1;
+    double *phi = (double *)malloc(sizeof(double) * (size_t)E * (size_t)(J - 1));
+    double Z[ORC_ION_MAX_STAGES], f[ORC_ION_MAX_STAGES];
+    for (int32_t s = 0; s < S; ++s) {
+        const double T = t_rad[s], W = w[s];
+        const double kT = K_BOLTZ * T;
+        const double x = ((2.0 * PI_D) * M_ELECTRON * kT) / (H_PLANCK * H_PLANCK);
+        const double saha = x * sqrt(x);
+        const double neb = (mode == 2) ? sqrt(0.9) : 1.0;  /* (T_e / T_R)^(1/2) */
+        double max_charge = 0.0;
+        for (int32_t e = 0; e < E; ++e) {
+            for (int32_t j = 0; j < J; ++j) {
+                int32_t a = ion_of[e * J + j];
+                double z = 1.0;
+                if (a >= 0) {
+                    z = 0.0;
+                    for (int32_t k = 0; k < K; ++k) {
+                        size_t lv = (size_t)a * K + k;
+                        z = z + g[lv] * orc_exp(-((energy_ev[lv] * EV_ERG) / kT));
+                    }
+                }
+                Z[j] = z;
+            }
+            for (int32_t j = 0; j + 1 < J; ++j) {
+                size_t t = (size_t)e * (J - 1) + j;
+                double p = ((2.0 * Z[j + 1]) / Z[j]) * saha * orc_exp(-((chi_ev[t] * EV_ERG) / kT));
+                if (mode == 2) p = ((W * (delta * zeta[t] + W * (1.0 - zeta[t]))) * neb) * p;
+                phi[t] = p;
+            }
+            max_charge += n_element[(size_t)s * E + e] * (double)(J - 1);
+        }
+        /* bisection on ln n_e: charge(lo) > lo, charge(hi) <= hi */
+        double lo = max_charge * 1e-40, hi = max_charge;
+        for (int it = 0; it < 200 && max_charge > 0.0; ++it) {
+            double mid = sqrt(lo * hi);
+            if (!(mid > lo && mid < hi)) break;
+            double charge = 0.0;
+            for (int32_t e = 0; e < E; ++e) {
+                stage_fractions(J, &phi[(size_t)e * (J - 1)], mid, f);
+                double ce = 0.0;
+                for (int32_t j = 1; j < J; ++j) ce += (double)j * f[j];
+                charge += n_element[(size_t)s * E + e] * ce;
+            }
+            if (charge > mid) lo = mid; else hi = mid;
+        }
+        const double ne = (max_charge > 0.0) ? sqrt(lo * hi) : 0.0;
+        n_e[s] = ne;
+        for (int32_t e = 0; e < E; ++e) {
+            if (ne > 0.0) stage_fractions(J, &phi[(size_t)e * (J - 1)], ne, f);
+            else { f[0] = 1.0; for (int32_t j = 1; j < J; ++j) f[j] = 0.0; }
+            for (int32_t j = 0; j < J; ++j) {
+                int32_t a = ion_of[e * J + j];
+                if (a >= 0) n_ion[(size_t)s * I + a] = n_element[(size_t)s * E + e] * f[j];
+            }
+        }
+    }
+    free(phi);
+    return 0;
+}

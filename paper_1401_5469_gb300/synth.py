@@ -73,6 +73,17 @@ class ModelSpec:
     ma_jump_offset: Optional[np.ndarray] = None  # [rows + 1] CSR over the rows
     ma_jump_target: Optional[np.ndarray] = None  # [n] row jumped to
     ma_jump_cdf: Optional[np.ndarray] = None     # [n] cumulative target probability (row ends at 1)
+    # ionization balance (Sect. 2.3): 0 fixed ion densities (n_ion), 1 lte (Eq. 2),
+    # 2 nebular (Eq. 3); ions with levels belong to (element, stage)
+    ionization_mode: int = 0
+    n_elements: int = 0
+    n_stages: int = 0                       # stages per element, the last one bare
+    ion_element: Optional[np.ndarray] = None  # [I]
+    ion_stage: Optional[np.ndarray] = None    # [I]
+    chi_ev: Optional[np.ndarray] = None       # [E, n_stages - 1] ionization potentials, eV
+    zeta: Optional[np.ndarray] = None         # [E, n_stages - 1] fraction of recombinations to ground
+    delta: float = 1.0
+    n_element: Optional[np.ndarray] = None    # [S, E] element number densities, cm^-3
     line_mode: int = 0          # 0 scatter, 1 downbranch, 2 macro-atom
     j_blue: bool = False
     spec_bins: int = 1000
@@ -217,6 +228,45 @@ def macroatom_table(rng, dbr_offset, n_ions: int, n_levels: int, p_jump_max: flo
     target = np.concatenate(targets).astype(np.int32) if targets else np.zeros(0, np.int32)
     cdf = np.concatenate(cdfs) if cdfs else np.zeros(0)
     return p, offset, target, cdf
+
+
+def ionization_data(rng, n_elements: int, n_levels_stages: int):
+    """Synthetic ionization data (the paper's come from NIST and its atomic
+    database): each element has n_levels_stages stages with levels plus a
+    bare top stage; ionization potentials rise with the stage (U(6, 12),
+    U(15, 25), U(30, 45), then +15 eV per stage), zeta ~ U(0.1, 0.9)."""
+    J1 = n_levels_stages
+    chi = np.zeros((n_elements, J1))
+    lo, hi = [6.0, 15.0, 30.0], [12.0, 25.0, 45.0]
+    for j in range(J1):
+        a = lo[j] if j < 3 else 30.0 + 15.0 * (j - 2)
+        b = hi[j] if j < 3 else 45.0 + 15.0 * (j - 2)
+        chi[:, j] = rng.uniform(a, b, size=n_elements)
+    zeta = rng.uniform(0.1, 0.9, size=(n_elements, J1))
+    return chi, zeta
+
+
+def nebular_model(mode: int = 2, stages: int = 3, **kw) -> ModelSpec:
+    """The downbranch model with its ions grouped into elements (ion a is stage
+    a % stages of element a // stages) and the ion densities from the
+    ionization balance (mode 1 lte, Eq. 2; 2 nebular, Eq. 3) instead of fixed
+    values; the electron density follows from charge conservation.  Element
+    totals keep the fixed-ion model's total heavy-element density."""
+    spec = downbranch_model(**kw)
+    I, S = int(spec.n_ions), spec.n_shells
+    if I % stages:
+        raise ValueError("n_ions must be a multiple of stages")
+    E = I // stages
+    rng = np.random.default_rng(int(kw.get("seed", 1401)) + 11)
+    spec.chi_ev, spec.zeta = ionization_data(rng, E, stages)
+    spec.ionization_mode = int(mode)
+    spec.n_elements, spec.n_stages = E, stages + 1
+    spec.ion_element = (np.arange(I) // stages).astype(np.int32)
+    spec.ion_stage = (np.arange(I) % stages).astype(np.int32)
+    per_ion = spec.n_ion.reshape(S, I)
+    spec.n_element = np.ascontiguousarray(per_ion.reshape(S, E, stages).sum(axis=2))
+    spec.name = "nebular" if mode == 2 else "lte-ionization"
+    return spec
 
 
 def macroatom_model(p_jump_max: float = 0.5, **kw) -> ModelSpec:

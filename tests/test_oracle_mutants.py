@@ -74,6 +74,15 @@ MUTANTS = [
     ("macro-atom jump decision inverted", "if (!(za < m->ma_jump_p[row])) break;",
      "if (za < m->ma_jump_p[row]) break;", 1,
      "tests/test_oracle_macroatom.py::test_walks_match_the_absorbing_markov_chain"),
+    ("nebular ratio without (T_e/T_R)^(1/2)", "const double neb = (mode == 2) ? sqrt(0.9) : 1.0;",
+     "const double neb = 1.0;", 1,
+     "tests/test_oracle_ionization.py::test_hydrogen_like_element_matches_the_saha_quadratic"),
+    ("Saha ratio with the partition functions inverted", "((2.0 * Z[j + 1]) / Z[j])",
+     "((2.0 * Z[j]) / Z[j + 1])", 1,
+     "tests/test_oracle_ionization.py::test_hydrogen_like_element_matches_the_saha_quadratic"),
+    ("charge counted one stage low", "for (int32_t j = 1; j < J; ++j) ce += (double)j * f[j];",
+     "for (int32_t j = 1; j < J; ++j) ce += (double)(j - 1) * f[j];", 1,
+     "tests/test_oracle_ionization.py::test_element_and_charge_conservation"),
     ("macro-atom jump target off by one", "if (zb < m->ma_jump_cdf[k]) { next = m->ma_jump_target[k]; break; }",
      "if (zb < m->ma_jump_cdf[k]) { next = m->ma_jump_target[k > b ? k - 1 : k]; break; }", 1,
      "tests/test_oracle_macroatom.py::test_walks_match_the_absorbing_markov_chain"),
