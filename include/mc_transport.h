@@ -55,6 +55,12 @@ typedef int32_t mc_status;
                                 (ma_jump_* tables), then re-emission via the branching
                                 table of the level it deactivates from */
 
+/* Ionization balance (Sect. 2.3), mc_atomic_desc.ionization_mode. */
+#define MC_ION_FIXED 0   /* ion densities and n_e as given */
+#define MC_ION_SAHA 1    /* Saha equation at T_R (Eq. 2) */
+#define MC_ION_NEBULAR 2 /* modified nebular approximation (Eq. 3), T_e = 0.9 T_R */
+#define MC_ION_MAX_STAGES 16
+
 /* Precision modes. */
 #define MC_PRECISION_FP64 0  /* all transport arithmetic in binary64 */
 #define MC_PRECISION_MIXED 1 /* distances and optical depths in binary32; comoving
@@ -106,7 +112,7 @@ typedef struct {
     const double *energy_ev;   /* [I*K] excitation energy above the ion ground state, eV */
     const double *g;           /* [I*K] statistical weights, > 0 */
     const uint8_t *metastable; /* [I*K] 1 = ground/metastable (Eq. 4), 0 = diluted (Eq. 5) */
-    const double *n_ion;       /* [S*I] ion number densities, cm^-3 */
+    const double *n_ion;       /* [S*I] ion number densities, cm^-3 (may be NULL in an ionization mode) */
     const uint32_t *dbr_offset;/* [I*K + 1] or NULL (scatter mode) */
     const uint32_t *dbr_line;  /* [nnz] line index of each branch */
     const double *dbr_cdf;     /* [nnz] cumulative branching ratio within the row */
@@ -123,6 +129,27 @@ typedef struct {
     const uint32_t *ma_jump_offset;   /* [I*K + 1] */
     const int32_t *ma_jump_target;    /* [n] */
     const double *ma_jump_cdf;        /* [n] */
+    /* Ionization balance (Sect. 2.3, Eqs. 2-3).  With MC_ION_SAHA or
+     * MC_ION_NEBULAR every recomputation of the Sobolev depths first solves,
+     * per shell at its T_R and W, for the stage fractions of each element and
+     * the electron density that conserve charge (n_e = sum over elements and
+     * stages of stage number x stage density), and replaces n_ion (which may
+     * then be NULL) and the geometry's n_e -- hence the Thomson opacity -- by
+     * the solution.  Partition functions: sum over the ion's levels of
+     * g exp(-E/kT_R); a stage without an ion (in particular the bare top stage
+     * J-1) has Z = 1.  Nebular mode scales Saha's Phi by
+     * W [delta zeta + W (1 - zeta)] (T_e/T_R)^(1/2) with T_e = 0.9 T_R.
+     * Given Sobolev depths (mc_set_plasma with tau) leave n_e and n_ion as
+     * they are. */
+    int32_t ionization_mode;          /* MC_ION_* */
+    uint32_t n_elements, n_stages;    /* E >= 1; 2 <= J <= MC_ION_MAX_STAGES */
+    const int32_t *ion_element;       /* [I] element of each ion, in [0, E) */
+    const int32_t *ion_stage;         /* [I] its stage in [0, J-1); (element, stage) pairs distinct */
+    const double *chi_ev;             /* [E*(J-1)] ionization potential of stage j, eV, > 0 */
+    const double *zeta;               /* [E*(J-1)] recombination fraction to the ground state,
+                                         in [0, 1] (nebular mode; else may be NULL) */
+    double delta;                     /* Eq. 3 delta, > 0 (nebular mode) */
+    const double *n_element;          /* [S*E] element number densities, cm^-3, >= 0 */
 } mc_atomic_desc;
 
 /* Run options. */
@@ -233,6 +260,14 @@ mc_status mc_read_packets(mc_model *m, uint64_t first, uint64_t count, int32_t *
 /* Read the device-side plasma state: t_rad[S], w[S], tau[S*L] (shell-major,
  * binary64 even in mixed mode).  Recomputes tau first if it is stale. */
 mc_status mc_read_plasma(mc_model *m, double *t_rad, double *w, double *tau);
+
+/* Read the electron densities n_e[S] (cm^-3) and ion densities n_ion[S*I]
+ * the transport uses: the solution of the ionization balance at the current
+ * T_R and W (recomputed first if stale) in an ionization mode, else the
+ * given values.  Either output may be NULL.  Synchronises.
+ *  Errors: MC_ERR_NOT_READY (no plasma set), MC_ERR_INVALID_ARG (n_ion
+ *  without atomic data). */
+mc_status mc_read_ionization(mc_model *m, double *n_e, double *n_ion);
 
 /* Device times of the last run, from CUDA events on the model's stream:
  * ms[0] Sobolev-depth recomputation (0 if none), ms[1] transport,

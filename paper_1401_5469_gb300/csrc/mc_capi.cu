@@ -95,7 +95,27 @@ mc_status recompute_tau(mc_model *m) {
   pp.line_gratio = m->line_gratio;
   pp.tau = m->tau;
   pp.tau32 = m->tau32;
-  cudaError_t e = launch_populations(pp, m->stream);
+  cudaError_t e = cudaSuccess;
+  if (m->ion_mode) {
+    IonParams ip{};
+    ip.S = pp.S; ip.I = pp.I; ip.K = pp.K;
+    ip.E = m->ion_E; ip.J = m->ion_J;
+    ip.mode = m->ion_mode;
+    ip.t_rad = m->t_rad; ip.w = m->w;
+    ip.eps_erg = m->eps_erg; ip.g = m->g;
+    ip.ion_of = m->ion_of;
+    ip.chi_erg = m->chi_erg; ip.zeta = m->zeta;
+    ip.delta = m->ion_delta;
+    ip.n_element = m->n_element;
+    ip.phi = m->ion_phi;
+    ip.n_ion = m->n_ion; ip.n_e = m->n_e;
+    ip.kappa = m->kappa; ip.inv_kappa = m->inv_kappa; ip.shell32 = m->shell32;
+    ip.t_exp = m->t_exp;
+    e = launch_ionization(ip, m->stream);
+    if (e != cudaSuccess) return cuda_fail(m, e, "ionization kernels");
+    m->launches += 2;
+  }
+  e = launch_populations(pp, m->stream);
   if (e == cudaSuccess) e = launch_sobolev_tau(pp, m->stream);
   if (e != cudaSuccess) return cuda_fail(m, e, "Sobolev-depth kernels");
   m->launches += 2;
@@ -182,14 +202,51 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
     return fail(nullptr, MC_ERR_INVALID_ARG, "macro-atom mode needs the ma_jump_* tables");
   uint32_t I = 0, K = 0;
   uint64_t nnz = 0;
+  const int32_t ion_mode = atomic ? atomic->ionization_mode : MC_ION_FIXED;
+  std::vector<int32_t> ion_of;  // [E*J] ion of each (element, stage), -1 none
   if (atomic) {
     I = atomic->n_ions;
     K = atomic->n_levels;
-    if (I == 0 || K == 0 || !atomic->energy_ev || !atomic->g || !atomic->metastable || !atomic->n_ion)
+    if (ion_mode != MC_ION_FIXED && ion_mode != MC_ION_SAHA && ion_mode != MC_ION_NEBULAR)
+      return fail(nullptr, MC_ERR_INVALID_ARG, "ionization_mode must be MC_ION_FIXED, MC_ION_SAHA or MC_ION_NEBULAR");
+    if (I == 0 || K == 0 || !atomic->energy_ev || !atomic->g || !atomic->metastable ||
+        (!atomic->n_ion && ion_mode == MC_ION_FIXED))
       return fail(nullptr, MC_ERR_INVALID_ARG, "atomic data needs n_ions, n_levels, energies, g, metastable, n_ion");
     if (!finite_nonneg(atomic->energy_ev, static_cast<size_t>(I) * K) ||
-        !finite_nonneg(atomic->n_ion, static_cast<size_t>(S) * I))
+        (atomic->n_ion && !finite_nonneg(atomic->n_ion, static_cast<size_t>(S) * I)))
       return fail(nullptr, MC_ERR_INVALID_ARG, "level energies and ion densities must be finite and >= 0");
+    if (ion_mode != MC_ION_FIXED) {
+      const uint32_t E = atomic->n_elements, J = atomic->n_stages;
+      if (E == 0 || J < 2 || J > MC_ION_MAX_STAGES || !atomic->ion_element || !atomic->ion_stage ||
+          !atomic->chi_ev || !atomic->n_element || (ion_mode == MC_ION_NEBULAR && !atomic->zeta))
+        return fail(nullptr, MC_ERR_INVALID_ARG,
+                    "ionization needs n_elements >= 1, 2 <= n_stages <= 16, ion_element, ion_stage, chi_ev, "
+                    "n_element (and zeta in nebular mode)");
+      if (static_cast<uint64_t>(S) * E * J >= (1ull << 31))
+        return fail(nullptr, MC_ERR_INVALID_ARG, "too many shells x elements x stages");
+      ion_of.assign(static_cast<size_t>(E) * J, -1);
+      for (uint32_t a = 0; a < I; ++a) {
+        const int32_t e = atomic->ion_element[a], j = atomic->ion_stage[a];
+        if (e < 0 || static_cast<uint32_t>(e) >= E || j < 0 || static_cast<uint32_t>(j) + 1 >= J)
+          return fail(nullptr, MC_ERR_INVALID_ARG, "ion_element/ion_stage out of range (the top stage is bare)");
+        int32_t &slot = ion_of[static_cast<size_t>(e) * J + j];
+        if (slot >= 0) return fail(nullptr, MC_ERR_INVALID_ARG, "two ions hold the same (element, stage)");
+        slot = static_cast<int32_t>(a);
+      }
+      const size_t EJ1 = static_cast<size_t>(E) * (J - 1);
+      for (size_t t = 0; t < EJ1; ++t)
+        if (!(atomic->chi_ev[t] > 0.0) || !std::isfinite(atomic->chi_ev[t]))
+          return fail(nullptr, MC_ERR_INVALID_ARG, "ionization potentials must be positive and finite");
+      if (ion_mode == MC_ION_NEBULAR) {
+        for (size_t t = 0; t < EJ1; ++t)
+          if (!(atomic->zeta[t] >= 0.0 && atomic->zeta[t] <= 1.0))
+            return fail(nullptr, MC_ERR_INVALID_ARG, "zeta must be in [0, 1]");
+        if (!(atomic->delta > 0.0) || !std::isfinite(atomic->delta))
+          return fail(nullptr, MC_ERR_INVALID_ARG, "delta must be positive and finite");
+      }
+      if (!finite_nonneg(atomic->n_element, static_cast<size_t>(S) * E))
+        return fail(nullptr, MC_ERR_INVALID_ARG, "element densities must be finite and >= 0");
+    }
     for (size_t a = 0; a < static_cast<size_t>(I) * K; ++a)
       if (!(atomic->g[a] > 0.0)) return fail(nullptr, MC_ERR_INVALID_ARG, "statistical weights must be > 0");
     if (meta) {
@@ -310,6 +367,17 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
       ok = alloc_n(m, &m->dbr_rec, nnz) && alloc_n(m, &m->dbr_bucket, nnz) &&
            alloc_n(m, &m->row_info, L);
   }
+  if (ok) ok = alloc_n(m, &m->n_e, S);
+  if (ok && ion_mode != MC_ION_FIXED) {
+    const size_t E = atomic->n_elements, J = atomic->n_stages;
+    m->ion_mode = ion_mode;
+    m->ion_E = static_cast<int32_t>(E);
+    m->ion_J = static_cast<int32_t>(J);
+    m->ion_delta = ion_mode == MC_ION_NEBULAR ? atomic->delta : 0.0;
+    ok = alloc_n(m, &m->ion_of, E * J) && alloc_n(m, &m->chi_erg, E * (J - 1)) &&
+         alloc_n(m, &m->zeta, E * (J - 1)) && alloc_n(m, &m->n_element, S * E) &&
+         alloc_n(m, &m->ion_phi, S * E * (J - 1));
+  }
   if (ok && run->record_packets) {
     const size_t n = run->max_packets;
     ok = alloc_n(m, &m->rec_status, n) && alloc_n(m, &m->rec_nu, n) && alloc_n(m, &m->rec_e, n) &&
@@ -353,6 +421,7 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
   chk(upload(m, m->inv_x_out, ixo.data(), S));
   chk(upload(m, m->kappa, kap.data(), S));
   chk(upload(m, m->inv_kappa, ikap.data(), S));
+  chk(upload(m, m->n_e, geom->n_e, S));
   std::vector<float> sh32;
   if (m->shell32) {
     sh32.resize(4 * static_cast<size_t>(S));
@@ -375,7 +444,18 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
     chk(upload(m, m->eps_erg, eps.data(), IK));
     chk(upload(m, m->g, atomic->g, IK));
     chk(upload(m, m->meta, atomic->metastable, IK));
-    chk(upload(m, m->n_ion, atomic->n_ion, static_cast<size_t>(S) * I));
+    if (atomic->n_ion) chk(upload(m, m->n_ion, atomic->n_ion, static_cast<size_t>(S) * I));
+    else chk(cudaMemsetAsync(m->n_ion, 0, static_cast<size_t>(S) * I * sizeof(double), m->stream));
+    if (m->ion_mode) {
+      const size_t E = atomic->n_elements, EJ1 = E * (atomic->n_stages - 1);
+      std::vector<double> chi(EJ1), zeta(EJ1, 0.0);
+      for (size_t t = 0; t < EJ1; ++t) chi[t] = atomic->chi_ev[t] * kEv;
+      if (atomic->zeta) zeta.assign(atomic->zeta, atomic->zeta + EJ1);
+      chk(upload(m, m->ion_of, ion_of.data(), ion_of.size()));
+      chk(upload(m, m->chi_erg, chi.data(), EJ1));
+      chk(upload(m, m->zeta, zeta.data(), EJ1));
+      chk(upload(m, m->n_element, atomic->n_element, static_cast<size_t>(S) * E));
+    }
     if (atomic->dbr_offset) {
       chk(upload(m, m->dbr_offset, atomic->dbr_offset, IK + 1));
       chk(upload(m, m->dbr_line, atomic->dbr_line, nnz));
@@ -592,7 +672,7 @@ void model_fill_transport(const mc_model *m, TransportParams &p, uint64_t seed, 
   p.x_in = m->x_in; p.x_out = m->x_out; p.inv_x_in = m->inv_x_in; p.inv_x_out = m->inv_x_out;
   p.inv_kappa = m->inv_kappa; p.row_info = m->row_info; p.dbr_rec = m->dbr_rec;
   p.dbr_bucket = m->dbr_bucket;
-  p.kappa = m->kappa; p.kappa32 = m->kappa32; p.x_in32 = m->x_in32; p.x_out32 = m->x_out32;
+  p.kappa = m->kappa;
   p.nu = m->nu; p.tau = m->tau; p.tau32 = m->tau32;
   p.line_row = m->line_row; p.dbr_offset = m->dbr_offset; p.dbr_line = m->dbr_line; p.dbr_cdf = m->dbr_cdf;
   p.j_est = m->j_est; p.nu_bar = m->nu_bar; p.j_blue = m->j_blue; p.spectrum = m->spectrum;
@@ -817,6 +897,24 @@ mc_status mc_read_plasma(mc_model *m, double *t_rad, double *w, double *tau) {
   if (e != cudaSuccess) return cuda_fail(m, e, "read plasma");
   if (tau && m->tau32)
     for (size_t i = 0; i < SL; ++i) tau[i] = static_cast<double>(t32[i]);
+  return MC_OK;
+}
+
+mc_status mc_read_ionization(mc_model *m, double *n_e, double *n_ion) {
+  if (!m) return MC_ERR_INVALID_ARG;
+  if (!m->plasma_set) return fail(m, MC_ERR_NOT_READY, "mc_set_plasma has not been called");
+  if (n_ion && !m->n_ion) return fail(m, MC_ERR_INVALID_ARG, "no atomic data: no ion densities");
+  if (m->ion_mode && !m->tau_given && m->tau_dirty) {
+    mc_status st = recompute_tau(m);
+    if (st != MC_OK) return st;
+  }
+  cudaError_t e = cudaSuccess;
+  if (n_e) e = cudaMemcpyAsync(n_e, m->n_e, m->S * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess && n_ion)
+    e = cudaMemcpyAsync(n_ion, m->n_ion, static_cast<size_t>(m->S) * m->I * sizeof(double),
+                        cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return cuda_fail(m, e, "read ionization");
   return MC_OK;
 }
 

@@ -63,8 +63,6 @@ struct TransportParams {
   const double *x_in, *x_out;        // [S] radii in units of c t_exp
   const double *inv_x_in, *inv_x_out;// [S]
   const double *kappa;               // [S] sigma_T n_e c t_exp (per unit x)
-  const float *kappa32;              // [S] same, binary32 (mixed mode)
-  const float *x_in32, *x_out32;     // [S] binary32 radii (mixed mode)
   const double *nu;                  // [L] line frequencies, descending
   const double *tau;                 // [S*L] Sobolev depths (fp64 mode)
   const float *tau32;                // [S*L] Sobolev depths (mixed mode)
@@ -137,6 +135,27 @@ struct PlasmaParams {
   float *tau32;                      // [S*L] or nullptr
 };
 
+// Ionization balance (Sect. 2.3, Eqs. 2-3) of S shells, E elements of J
+// stages each; ion_of[e*J + j] is the ion holding stage j of element e, or -1
+// (partition function 1).  Writes n_ion, n_e and the Thomson opacity arrays.
+struct IonParams {
+  int32_t S, I, K, E, J;
+  int32_t mode;                      // 1 Saha (Eq. 2), 2 modified nebular (Eq. 3)
+  const double *t_rad, *w;           // [S]
+  const double *eps_erg, *g;         // [I*K]
+  const int32_t *ion_of;             // [E*J]
+  const double *chi_erg, *zeta;      // [E*(J-1)]
+  double delta;
+  const double *n_element;           // [S*E]
+  double *phi;                       // [S*E*(J-1)] scratch: n_{j+1} n_e / n_j
+  double *n_ion;                     // [S*I]
+  double *n_e;                       // [S]
+  double *kappa, *inv_kappa;         // [S] sigma_T n_e c t_exp and its inverse (0 if kappa = 0)
+  float *shell32;                    // [4S] or nullptr: binary32 copies at 2S (kappa), 3S (inverse)
+  double t_exp;                      // s (kappa = ((sigma_T n_e) c) t_exp)
+};
+constexpr int kIonMaxStages = 16;
+
 struct UpdateParams {
   int32_t S;
   const double *j_est, *nu_bar, *norm;
@@ -162,6 +181,7 @@ cudaError_t launch_to_f32(const double *in, float *out, size_t n, cudaStream_t s
 // j_est = fix[s] 2^-32 E, nu_bar = fix[S + s] 2^-32 E nu_ref (mixed precision).
 cudaError_t launch_est_from_fix(const unsigned long long *fix, int S, double e_cmf, double nu_ref,
                                 double *j_est, double *nu_bar, cudaStream_t st);
+cudaError_t launch_ionization(const IonParams &p, cudaStream_t st);  // two kernels
 cudaError_t launch_populations(const PlasmaParams &p, cudaStream_t st);
 cudaError_t launch_sobolev_tau(const PlasmaParams &p, cudaStream_t st);
 cudaError_t launch_update(const UpdateParams &p, cudaStream_t st);

@@ -39,7 +39,6 @@ struct mc_model {
   mcgpu::MaRow *ma_row = nullptr;    // macro-atom levels (MC_LINE_MACROATOM)
   mcgpu::MaJump *ma_jump = nullptr;
   unsigned long long *row_info = nullptr;
-  float *kappa32 = nullptr, *x_in32 = nullptr, *x_out32 = nullptr;
   double *nu = nullptr, *tau = nullptr;
   float *tau32 = nullptr;
   int32_t *line_row = nullptr, *lev_l = nullptr, *lev_u = nullptr;
@@ -49,6 +48,12 @@ struct mc_model {
   double *t_rad = nullptr, *w = nullptr, *eps_erg = nullptr, *g = nullptr, *n_ion = nullptr,
          *pop = nullptr;
   uint8_t *meta = nullptr;
+  // Ionization balance (atomic ionization_mode != 0): inputs, scratch and n_e.
+  int32_t ion_mode = 0, ion_E = 0, ion_J = 0;
+  double ion_delta = 0.0;
+  int32_t *ion_of = nullptr;
+  double *chi_erg = nullptr, *zeta = nullptr, *n_element = nullptr, *ion_phi = nullptr;
+  double *n_e = nullptr;  // [S] electron densities the Thomson opacity is built from
   double *norm = nullptr;
   double *j_est = nullptr, *nu_bar = nullptr, *j_blue = nullptr, *spectrum = nullptr;
   double *spectrum_v = nullptr;  // [bins + 2] virtual-packet spectrum (allocated on first use)

@@ -1,6 +1,7 @@
-// Plasma-state kernels: level populations (Kerzendorf & Sim 2014, Sect. 2.3,
-// Eqs. 4-5), Sobolev optical depths (Eq. 12), the radiation-field update from
-// the Monte Carlo estimators (Eqs. 15-16) and estimator zeroing.
+// Plasma-state kernels: ionization balance and level populations (Kerzendorf
+// & Sim 2014, Sect. 2.3, Eqs. 2-5), Sobolev optical depths (Eq. 12), the
+// radiation-field update from the Monte Carlo estimators (Eqs. 15-16) and
+// estimator zeroing.
 #include <cstdint>
 
 #include "mc_internal.h"
@@ -29,6 +30,114 @@ __global__ void populations_kernel(const PlasmaParams p) {
   for (int k = 0; k < p.K; ++k) {
     const double wk = (p.lte_excitation || p.metastable[a0 + k]) ? 1.0 : w;
     out[k] = ((wk * p.g[a0 + k]) * exp(-(p.eps_erg[a0 + k] * inv_kT))) * scale;
+  }
+}
+
+// Partition function of ion `a` from its levels, sum_k g_k exp(-eps_k / k T_R)
+// (the populations of Eq. 4 summed); a stage without levels (a < 0) has 1.
+__device__ double ion_partition(const IonParams &p, int a, double inv_kT) {
+  if (a < 0) return 1.0;
+  const size_t a0 = static_cast<size_t>(a) * p.K;
+  double z = 0.0;
+  for (int k = 0; k < p.K; ++k) z += p.g[a0 + k] * exp(-(p.eps_erg[a0 + k] * inv_kT));
+  return z;
+}
+
+// One thread per (shell, element, stage j < J-1): Phi_j = n_{j+1} n_e / n_j
+// from the Saha equation (Eq. 2), 2 (Z_{j+1}/Z_j) (2 pi m_e k T / h^2)^(3/2)
+// exp(-chi_j / k T); in nebular mode (Eq. 3) times
+// W [delta zeta + W (1 - zeta)] (T_e / T_R)^(1/2) with T_e = 0.9 T_R.
+__global__ void ion_phi_kernel(const IonParams p) {
+  const int J1 = p.J - 1;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p.S * p.E * J1) return;
+  const int s = idx / (p.E * J1);
+  const int t = idx - s * (p.E * J1);
+  const int e = t / J1, j = t - e * J1;
+  const double kT = kKB * p.t_rad[s];
+  const double inv_kT = 1.0 / kT;
+  const double x = ((2.0 * kPi) * kMe * kT) / (kH * kH);
+  const double saha = x * sqrt(x);
+  const double z_lo = ion_partition(p, p.ion_of[e * p.J + j], inv_kT);
+  const double z_hi = ion_partition(p, p.ion_of[e * p.J + j + 1], inv_kT);
+  double phi = ((2.0 * z_hi) / z_lo) * saha * exp(-(p.chi_erg[t] * inv_kT));
+  if (p.mode == 2) {
+    const double W = p.w[s], z = p.zeta[t];
+    phi = ((W * (p.delta * z + W * (1.0 - z))) * sqrt(0.9)) * phi;
+  }
+  p.phi[idx] = phi;
+}
+
+// Stage fractions of one element at electron density n_e: n_j / N from the
+// ratios Phi_j / n_e (each stage relative to the one below).
+__device__ void stage_fractions(int J, const double *phi, double n_e, double *f) {
+  double r = 1.0, sum = 1.0;
+  f[0] = 1.0;
+  for (int j = 1; j < J; ++j) {
+    r = r * (phi[j - 1] / n_e);
+    f[j] = r;
+    sum += r;
+  }
+  for (int j = 0; j < J; ++j) f[j] = f[j] / sum;
+}
+
+// Sum over the warp, the same value in every lane (lane 0's, broadcast).
+__device__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// One warp per shell, lanes over elements: charge conservation,
+// n_e = sum_e N_e sum_j j f_j(n_e), solved by bisection on ln n_e between
+// 1e-40 and 1 times the charge of full ionization (charge(n_e) - n_e falls
+// monotonically); then the ion densities N_e f_j, n_e and the Thomson opacity.
+__global__ void ion_balance_kernel(const IonParams p) {
+  const int s = static_cast<int>((blockIdx.x * static_cast<unsigned>(blockDim.x) + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= p.S) return;  // whole warps: blockDim is a multiple of 32
+  const int E = p.E, J = p.J, J1 = J - 1;
+  const double *phi = p.phi + static_cast<size_t>(s) * E * J1;
+  const double *n_el = p.n_element + static_cast<size_t>(s) * E;
+  double part = 0.0;
+  for (int e = lane; e < E; e += 32) part += n_el[e] * static_cast<double>(J1);
+  const double max_charge = warp_sum(part);
+  double f[kIonMaxStages];
+  double lo = max_charge * 1e-40, hi = max_charge;
+  for (int it = 0; it < 200 && max_charge > 0.0; ++it) {
+    const double mid = sqrt(lo * hi);
+    if (!(mid > lo && mid < hi)) break;
+    double c = 0.0;
+    for (int e = lane; e < E; e += 32) {
+      stage_fractions(J, phi + e * J1, mid, f);
+      double ce = 0.0;
+      for (int j = 1; j < J; ++j) ce += static_cast<double>(j) * f[j];
+      c += n_el[e] * ce;
+    }
+    if (warp_sum(c) > mid) lo = mid; else hi = mid;
+  }
+  const double ne = (max_charge > 0.0) ? sqrt(lo * hi) : 0.0;
+  for (int e = lane; e < E; e += 32) {
+    if (ne > 0.0) {
+      stage_fractions(J, phi + e * J1, ne, f);
+    } else {
+      f[0] = 1.0;
+      for (int j = 1; j < J; ++j) f[j] = 0.0;
+    }
+    for (int j = 0; j < J; ++j) {
+      const int a = p.ion_of[e * J + j];
+      if (a >= 0) p.n_ion[static_cast<size_t>(s) * p.I + a] = n_el[e] * f[j];
+    }
+  }
+  if (lane == 0) {
+    const double kap = ((kSigmaT * ne) * kC) * p.t_exp;
+    const double ikap = kap > 0.0 ? 1.0 / kap : 0.0;
+    p.n_e[s] = ne;
+    p.kappa[s] = kap;
+    p.inv_kappa[s] = ikap;
+    if (p.shell32) {
+      p.shell32[2 * p.S + s] = static_cast<float>(kap);
+      p.shell32[3 * p.S + s] = kap > 0.0 ? static_cast<float>(1.0 / kap) : 0.0f;
+    }
   }
 }
 
@@ -190,6 +299,16 @@ int sm_count() {
 }
 
 }  // namespace
+
+cudaError_t launch_ionization(const IonParams &p, cudaStream_t st) {
+  if (p.J < 2 || p.J > kIonMaxStages) return cudaErrorInvalidValue;
+  const int n = p.S * p.E * (p.J - 1);
+  ion_phi_kernel<<<(n + 127) / 128, 128, 0, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ion_balance_kernel<<<(p.S + 3) / 4, 128, 0, st>>>(p);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_populations(const PlasmaParams &p, cudaStream_t st) {
   const int n = p.S * p.I;

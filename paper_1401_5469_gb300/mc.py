@@ -29,6 +29,7 @@ MC_WARN_CAPPED = 1
 MC_LINE_SCATTER, MC_LINE_DOWNBRANCH = 0, 1
 MC_PRECISION_FP64, MC_PRECISION_MIXED = 0, 1
 MC_LINE_SCATTER, MC_LINE_DOWNBRANCH, MC_LINE_MACROATOM = 0, 1, 2
+MC_ION_FIXED, MC_ION_SAHA, MC_ION_NEBULAR = 0, 1, 2
 MC_PACKET_ESCAPED, MC_PACKET_REABSORBED, MC_PACKET_CAPPED = 1, 2, 3
 MC_N_COUNTERS = 6
 COUNTER_NAMES = ("segments", "line_checks", "resonances", "line_interactions", "e_scatters",
@@ -38,6 +39,7 @@ COUNTER_NAMES = ("segments", "line_checks", "resonances", "line_interactions", "
 EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_run_iteration_range",
             "mc_update_radiation_field",
             "mc_read_estimators", "mc_read_spectrum", "mc_read_packets", "mc_read_plasma",
+            "mc_read_ionization",
             "mc_read_timing", "mc_read_transport_phases", "mc_launch_count", "mc_synchronize", "mc_model_destroy",
             "mc_status_string", "mc_last_error_message", "mc_transport_noalloc",
             "mc_batch_create", "mc_batch_run_iteration", "mc_batch_synchronize",
@@ -65,7 +67,10 @@ class mc_atomic_desc(C.Structure):
                 ("dbr_offset", C.c_void_p), ("dbr_line", C.c_void_p), ("dbr_cdf", C.c_void_p),
                 ("lte_excitation", C.c_int32),
                 ("ma_jump_p", C.c_void_p), ("ma_jump_offset", C.c_void_p), ("ma_jump_target", C.c_void_p),
-                ("ma_jump_cdf", C.c_void_p)]
+                ("ma_jump_cdf", C.c_void_p),
+                ("ionization_mode", C.c_int32), ("n_elements", C.c_uint32), ("n_stages", C.c_uint32),
+                ("ion_element", C.c_void_p), ("ion_stage", C.c_void_p), ("chi_ev", C.c_void_p),
+                ("zeta", C.c_void_p), ("delta", C.c_double), ("n_element", C.c_void_p)]
 
 
 class mc_run_desc(C.Structure):
@@ -168,6 +173,8 @@ def load(build_if_missing: bool = True):
     L.mc_read_packets.argtypes = [vp, u64, u64, vp, vp, vp, vp]
     L.mc_read_plasma.restype = i32
     L.mc_read_plasma.argtypes = [vp, vp, vp, vp]
+    L.mc_read_ionization.restype = i32
+    L.mc_read_ionization.argtypes = [vp, vp, vp]
     L.mc_read_timing.restype = i32
     L.mc_read_timing.argtypes = [vp, vp]
     L.mc_read_transport_phases.restype = i32
@@ -280,6 +287,10 @@ def mc_read_plasma(h, t_rad=None, w=None, tau=None):
     return _check(load().mc_read_plasma(h, _p(t_rad), _p(w), _p(tau)), h)
 
 
+def mc_read_ionization(h, n_e=None, n_ion=None):
+    return _check(load().mc_read_ionization(h, _p(n_e), _p(n_ion)), h)
+
+
 def mc_read_timing(h):
     ms = np.zeros(3, dtype=np.float32)
     _check(load().mc_read_timing(h, _p(ms)), h)
@@ -355,6 +366,40 @@ def _u32(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.uint32)
 
 
+def atomic_desc(spec, keep):
+    """The mc_atomic_desc of a ``synth.ModelSpec`` (None without atomic data);
+    the arrays it points to are appended to ``keep``."""
+    if spec.energy_ev is None:
+        return None
+    e, g = _f64(spec.energy_ev), _f64(spec.g)
+    meta = np.ascontiguousarray(spec.metastable, dtype=np.uint8)
+    nion = _f64(spec.n_ion) if spec.n_ion is not None else None
+    off, dl, cdf = _u32(spec.dbr_offset), _u32(spec.dbr_line), _f64(spec.dbr_cdf)
+    keep += [e, g, meta, nion, off, dl, cdf]
+    jp = jo = jt = jc = None
+    if getattr(spec, "ma_jump_p", None) is not None:
+        jp, jo = _f64(spec.ma_jump_p), _u32(spec.ma_jump_offset)
+        jt, jc = _i32(spec.ma_jump_target), _f64(spec.ma_jump_cdf)
+        keep += [jp, jo, jt, jc]
+    a = mc_atomic_desc(n_ions=int(spec.n_ions), n_levels=int(spec.n_levels),
+                       energy_ev=_p(e), g=_p(g), metastable=_p(meta),
+                       n_ion=_p(nion), dbr_offset=_p(off), dbr_line=_p(dl),
+                       dbr_cdf=_p(cdf), lte_excitation=0,
+                       ma_jump_p=_p(jp), ma_jump_offset=_p(jo),
+                       ma_jump_target=_p(jt), ma_jump_cdf=_p(jc))
+    mode = int(getattr(spec, "ionization_mode", 0) or 0)
+    if mode:
+        ie, ist = _i32(spec.ion_element), _i32(spec.ion_stage)
+        chi, nel = _f64(spec.chi_ev), _f64(spec.n_element)
+        zeta = _f64(spec.zeta) if spec.zeta is not None else None
+        keep += [ie, ist, chi, zeta, nel]
+        a.ionization_mode, a.n_elements, a.n_stages = mode, int(spec.n_elements), int(spec.n_stages)
+        a.ion_element, a.ion_stage = _p(ie), _p(ist)
+        a.chi_ev, a.zeta, a.n_element = _p(chi), _p(zeta), _p(nel)
+        a.delta = float(spec.delta)
+    return a
+
+
 class Model:
     """One ejecta model resident on the GPU (wraps a ``synth.ModelSpec``)."""
 
@@ -374,24 +419,7 @@ class Model:
         k += [f, ion, lo, up]
         self.lines = mc_line_desc(n_lines=nu.size, nu=_p(nu), f=_p(f), ion=_p(ion), lower=_p(lo),
                                   upper=_p(up))
-        self.atomic = None
-        if spec.energy_ev is not None:
-            e, g = _f64(spec.energy_ev), _f64(spec.g)
-            meta = np.ascontiguousarray(spec.metastable, dtype=np.uint8)
-            nion = _f64(spec.n_ion)
-            off, dl, cdf = _u32(spec.dbr_offset), _u32(spec.dbr_line), _f64(spec.dbr_cdf)
-            k += [e, g, meta, nion, off, dl, cdf]
-            jp = jo = jt = jc = None
-            if getattr(spec, "ma_jump_p", None) is not None:
-                jp, jo = _f64(spec.ma_jump_p), _u32(spec.ma_jump_offset)
-                jt, jc = _i32(spec.ma_jump_target), _f64(spec.ma_jump_cdf)
-                k += [jp, jo, jt, jc]
-            self.atomic = mc_atomic_desc(n_ions=int(spec.n_ions), n_levels=int(spec.n_levels),
-                                         energy_ev=_p(e), g=_p(g), metastable=_p(meta),
-                                         n_ion=_p(nion), dbr_offset=_p(off), dbr_line=_p(dl),
-                                         dbr_cdf=_p(cdf), lte_excitation=0,
-                                         ma_jump_p=_p(jp), ma_jump_offset=_p(jo),
-                                         ma_jump_target=_p(jt), ma_jump_cdf=_p(jc))
+        self.atomic = atomic_desc(spec, k)
         jb = spec.j_blue if j_blue is None else j_blue
         mp = int(max_packets if max_packets is not None else spec.n_packets)
         self.run = mc_run_desc(line_mode=int(spec.line_mode), precision=int(precision),
@@ -401,6 +429,7 @@ class Model:
                                max_segments=int(max_segments), delta_t=1.0,
                                timeout_ns=int(timeout_ns))
         self.S, self.L = vi.size, nu.size
+        self.I = int(spec.n_ions) if self.atomic is not None else 0
         self.bins = int(spec.spec_bins)
         self.stream = stream if stream is not None else _torch_stream_handle()
         self._alloc = _TorchAllocator(self.stream) if use_torch_allocator else None
@@ -497,6 +526,14 @@ class Model:
         tau = np.zeros((self.S, self.L))
         mc_read_plasma(self.h, t, w, tau)
         return t, w, tau
+
+    def ionization(self):
+        """mc_read_ionization: electron densities [S] and ion densities [S, I]
+        the transport uses (the ionization balance in an ionization mode)."""
+        n_e = np.zeros(self.S)
+        n_ion = np.zeros((self.S, self.I)) if self.I else None
+        mc_read_ionization(self.h, n_e, n_ion)
+        return n_e, n_ion
 
     def timing(self):
         return mc_read_timing(self.h)

@@ -96,3 +96,75 @@ def test_t_inner_update_matches_the_oracle():
     import oracle
     for t, lr, le in ((9000.0, 4e42, 3.1e42), (12000.0, 1e41, 2e41), (8000.0, 1e42, 0.0)):
         assert mc.t_inner_update(t, lr, le) == oracle.t_inner_update(t, lr, le)
+
+
+def _full_descs(spec):
+    g, l, r, keep = _descs(spec, line_mode=int(spec.line_mode))
+    for name in ("f", "ion", "lower", "upper"):
+        a = getattr(spec, name)
+        arr = np.ascontiguousarray(a, np.float64 if name == "f" else np.int32)
+        keep.append(arr)
+        setattr(l, name, arr.ctypes.data)
+    a = mc.atomic_desc(spec, keep)
+    return g, l, a, r, keep
+
+
+@pytest.mark.parametrize("mutate,message", [
+    ("mode", "ionization_mode"),
+    ("one_stage", "ionization needs"),
+    ("too_many_stages", "ionization needs"),
+    ("bare_stage_ion", "out of range"),
+    ("duplicate", "same (element, stage)"),
+    ("chi", "ionization potentials"),
+    ("zeta", "zeta"),
+    ("no_zeta", "ionization needs"),
+    ("delta", "delta"),
+    ("n_element", "element densities"),
+    ("fixed_without_n_ion", "atomic data needs"),
+])
+def test_create_rejects_invalid_ionization_data(mutate, message):
+    spec = synth.nebular_model(mode=2, n_lines=300, n_shells=4, n_packets=10)
+    if mutate == "one_stage":
+        spec.n_stages = 1
+    elif mutate == "too_many_stages":
+        spec.n_stages = 17
+    elif mutate == "bare_stage_ion":
+        spec.ion_stage = spec.ion_stage.copy()
+        spec.ion_stage[0] = spec.n_stages - 1
+    elif mutate == "duplicate":
+        spec.ion_stage = spec.ion_stage.copy()
+        spec.ion_stage[1] = spec.ion_stage[0]
+    elif mutate == "chi":
+        spec.chi_ev = spec.chi_ev.copy()
+        spec.chi_ev[0, 1] = 0.0
+    elif mutate == "zeta":
+        spec.zeta = spec.zeta.copy()
+        spec.zeta[1, 0] = 1.5
+    elif mutate == "no_zeta":
+        spec.zeta = None
+    elif mutate == "delta":
+        spec.delta = 0.0
+    elif mutate == "n_element":
+        spec.n_element = spec.n_element.copy()
+        spec.n_element[2, 0] = -1.0
+    elif mutate == "fixed_without_n_ion":
+        spec.ionization_mode = 0
+        spec.n_ion = None
+    g, l, a, r, keep = _full_descs(spec)
+    if mutate == "mode":
+        a.ionization_mode = 3
+    L = mc.load()
+    h = C.c_void_p()
+    rc = L.mc_model_create(C.byref(g), C.byref(l), C.byref(a), C.byref(r), None, None, C.byref(h))
+    assert rc == mc.MC_ERR_INVALID_ARG
+    assert not h.value
+    assert message in L.mc_last_error_message(None).decode()
+
+
+def test_ionization_descriptor_matches_the_model():
+    spec = synth.nebular_model(mode=1, n_lines=300, n_shells=4, n_packets=10)
+    keep = []
+    a = mc.atomic_desc(spec, keep)
+    assert (a.ionization_mode, a.n_elements, a.n_stages) == (mc.MC_ION_SAHA, spec.n_elements, spec.n_stages)
+    assert a.n_element == keep[-1].ctypes.data and keep[-1].shape == (4, spec.n_elements)
+    assert a.delta == 1.0
