@@ -406,6 +406,15 @@ mc_status mc_batch_set_launch(mc_batch *b, const mc_batch_launch *launch);
 /* The launch shape in use, with blocks_per_sm resolved to the value used. */
 mc_status mc_batch_get_launch(const mc_batch *b, mc_batch_launch *launch);
 
+/* CUDA-graph capture of the batched iteration.  enable = 1 (the default):
+ * capture on the first call and replay while the shape is unchanged, as
+ * described at mc_batch_run_iteration; enable = 0: enqueue the kernels on the
+ * batch's stream directly every iteration (for tools that step through
+ * individual launches, or shapes that change every iteration).  No result
+ * depends on it.  Waits for the iteration in flight.
+ *  Errors: MC_ERR_INVALID_ARG (b NULL, enable not 0 or 1), MC_ERR_CUDA. */
+mc_status mc_batch_capture_graph(mc_batch *b, int32_t enable);
+
 /* Autotuner: pick the fastest launch shape for these iterations by timing
  * transport-only trial iterations (update = 0, the same arguments as
  * mc_batch_run_iteration).  Coordinate search: queue order, then block size,

@@ -19,6 +19,13 @@ Functions and the passage each follows:
 * ``log`` / ``exp``       -- own series (A&S 4.1.27; Cody & Waite 1980)
 * ``philox`` / ``uniforms`` -- Philox4x32-10 (Salmon et al. 2011) draw stream
 * ``distance_shell``      -- shell-crossing distance of Sect. 2.6
+* ``ionization_state``    -- ionization balance, Eqs. 2-3 (lte / nebular modes)
+* ``plasma_tau``          -- Eqs. 2-5 and 12 together (the plasma-state step)
+* ``virtual_tau``         -- optical depth of a virtual packet's ray (Sect. 2.9, Eq. 21)
+* ``macroatom_walks``     -- macro-atom internal jumps and deactivation (Sect. 2.5)
+* ``t_inner_from_luminosity`` / ``emitted_luminosity`` / ``t_inner_update``
+                          -- inner-boundary temperature (Sect. 2.8, Eq. 18)
+* ``run_loop``            -- the iteration cycle of Sect. 2.8 (resumable from T_R, W)
 
 Parity unpinned: the Philox stream is pinned only statistically (its published
 known-answer vectors are not available here); every other function has pins in
@@ -478,18 +485,20 @@ def plasma_tau(spec, t_rad, w):
 
 
 def run_loop(spec, n_iterations, n_packets, seed, threads=1, t_inner=None, record=False,
-             max_segments=1_000_000):
+             max_segments=1_000_000, t_rad=None, w=None, first_iteration=0):
     """The iteration cycle of Sect. 2.8 with T_R = 1e4 K and geometric W to
-    start, tau recomputed from the plasma each iteration and T_R, W updated
-    from the estimators after each.  Returns the per-iteration results."""
+    start (or the given T_R, W: a run resumed from a saved state), tau
+    recomputed from the plasma each iteration and T_R, W updated from the
+    estimators after each; iterations are numbered from first_iteration.
+    Returns the per-iteration results."""
     S = spec.n_shells
     t_in = spec.t_inner if t_inner is None else t_inner
-    t_rad = np.full(S, 1.0e4)
-    w = geometric_dilution(spec)
+    t_rad = np.full(S, 1.0e4) if t_rad is None else _f64(t_rad).copy()
+    w = geometric_dilution(spec) if w is None else _f64(w).copy()
     om = None
     out = []
     ionized = getattr(spec, "ionization_mode", 0) and spec.tau is None
-    for it in range(n_iterations):
+    for it in range(first_iteration, first_iteration + n_iterations):
         tau = plasma_tau(spec, t_rad, w) if spec.tau is None else spec.tau
         if om is None:
             om = OracleModel(spec, tau=tau, max_segments=max_segments)

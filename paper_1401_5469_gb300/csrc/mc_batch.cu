@@ -44,6 +44,8 @@ struct mc_batch {
   std::vector<double> graph_tin;      // per-model T_inner
   bool graph_update = false;
   uint64_t graph_total = 0;
+  bool use_graph = true;           // mc_batch_capture_graph
+  uint64_t iterations = 0;         // batched iterations enqueued (graph or direct)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
   uint64_t launches = 0, graph_launches = 0;
   std::string err;
@@ -74,8 +76,10 @@ void drop_graph(mc_batch *b) {
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
 }
 
-// Enqueue one iteration of every model on the batch stream.
-mc_status enqueue_iteration(mc_batch *b, int update) {
+// Enqueue one iteration of every model on the batch stream (`capturing`:
+// inside a stream capture, so the timing events become external event nodes).
+mc_status enqueue_iteration(mc_batch *b, int update, bool capturing) {
+  const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   for (mc_model *m : b->models) {
     const mc_status rc = model_prepare(m, b->stream, false);
     if (rc != MC_OK) return bfail(b, rc, m->err);
@@ -92,10 +96,10 @@ mc_status enqueue_iteration(mc_batch *b, int update) {
   p.n_packets = b->h_prefix[b->models.size()];
   p.work_counter = b->d_counters;
   p.flags = b->d_counters + 1;
-  e = cudaEventRecordWithFlags(b->t0, b->stream, cudaEventRecordExternal);
+  e = cudaEventRecordWithFlags(b->t0, b->stream, ev_flags);
   if (e == cudaSuccess) e = launch_transport_batch(p, b->line_mode, b->j_blue, b->record, b->grid,
                                                     static_cast<int>(b->block), b->stream);
-  if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->t1, b->stream, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(b->t1, b->stream, ev_flags);
   if (e != cudaSuccess) return bcuda(b, e, "batched transport");
   b->launches += 1;
   for (size_t k = 0; k < b->models.size(); ++k) {
@@ -173,9 +177,9 @@ mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, const uint3
                                  const uint64_t *n_packets, const double *t_inner, int32_t update) {
   if (!b || !seeds || !iterations || !n_packets || !t_inner) return MC_ERR_INVALID_ARG;
   const size_t n = b->models.size();
-  // the previous iteration's graph reads the pinned parameter table when it
-  // starts; wait until it has been copied before overwriting it
-  if (b->graph_launches) {
+  // the previous iteration reads the pinned parameter table when it starts;
+  // wait until it has been copied before overwriting it
+  if (b->iterations) {
     const cudaError_t ew = cudaEventSynchronize(b->t0);
     if (ew != cudaSuccess) return bcuda(b, ew, "previous iteration");
   }
@@ -231,38 +235,44 @@ mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, const uint3
 
   const std::vector<uint64_t> np(n_packets, n_packets + n);
   const std::vector<double> tin(t_inner, t_inner + n);
-  const bool reuse = b->exec && b->graph_shape == shape && b->graph_order == order &&
-                     b->graph_np == np && b->graph_tin == tin &&
-                     b->graph_update == (update != 0) &&
-                     b->graph_total == b->h_prefix[n];
-  if (!reuse) {
-    drop_graph(b);
-    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return bcuda(b, e, "begin capture");
-    const mc_status rc = enqueue_iteration(b, update);
-    cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(b->stream, &g);
-    if (rc != MC_OK) { if (g) cudaGraphDestroy(g); return rc; }
-    if (e != cudaSuccess) return bcuda(b, e, "end capture");
-    b->graph = g;
-    e = cudaGraphInstantiate(&b->exec, g, 0);
-    if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
-    b->graph_shape = shape;
-    b->graph_order = order;
-    b->graph_np = np;
-    b->graph_tin = tin;
-    b->graph_update = update != 0;
-    b->graph_total = b->h_prefix[n];
+  if (!b->use_graph) {
+    const mc_status rc = enqueue_iteration(b, update, false);
+    if (rc != MC_OK) return rc;
   } else {
-    // the captured steps mark the same state; keep the host-side flags in step
-    for (mc_model *m : b->models) {
-      m->ran_plasma = false;
-      if (!m->tau_given && m->tau_dirty) m->tau_dirty = false;
+    const bool reuse = b->exec && b->graph_shape == shape && b->graph_order == order &&
+                       b->graph_np == np && b->graph_tin == tin &&
+                       b->graph_update == (update != 0) &&
+                       b->graph_total == b->h_prefix[n];
+    if (!reuse) {
+      drop_graph(b);
+      e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return bcuda(b, e, "begin capture");
+      const mc_status rc = enqueue_iteration(b, update, true);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(b->stream, &g);
+      if (rc != MC_OK) { if (g) cudaGraphDestroy(g); return rc; }
+      if (e != cudaSuccess) return bcuda(b, e, "end capture");
+      b->graph = g;
+      e = cudaGraphInstantiate(&b->exec, g, 0);
+      if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
+      b->graph_shape = shape;
+      b->graph_order = order;
+      b->graph_np = np;
+      b->graph_tin = tin;
+      b->graph_update = update != 0;
+      b->graph_total = b->h_prefix[n];
+    } else {
+      // the captured steps mark the same state; keep the host-side flags in step
+      for (mc_model *m : b->models) {
+        m->ran_plasma = false;
+        if (!m->tau_given && m->tau_dirty) m->tau_dirty = false;
+      }
     }
+    e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "graph launch");
+    b->graph_launches += 1;
   }
-  e = cudaGraphLaunch(b->exec, b->stream);
-  if (e != cudaSuccess) return bcuda(b, e, "graph launch");
-  b->graph_launches += 1;
+  b->iterations += 1;
   for (size_t k = 0; k < n; ++k) {
     mc_model *m = b->models[k];
     m->have_run = true;
@@ -285,7 +295,7 @@ mc_status mc_batch_synchronize(mc_batch *b) {
 
 mc_status mc_batch_read_timing(mc_batch *b, float *ms) {
   if (!b || !ms) return MC_ERR_INVALID_ARG;
-  if (!b->graph_launches) return bfail(b, MC_ERR_NOT_READY, "no batched iteration yet");
+  if (!b->iterations) return bfail(b, MC_ERR_NOT_READY, "no batched iteration yet");
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e == cudaSuccess) e = cudaEventElapsedTime(ms, b->t0, b->t1);
   if (e != cudaSuccess) return bcuda(b, e, "batch timing");
@@ -299,7 +309,7 @@ mc_status mc_batch_set_launch(mc_batch *b, const mc_batch_launch *launch) {
   const uint32_t block = launch->block == 0 ? 128u : launch->block;
   if (block_slot(block) < 0) return bfail(b, MC_ERR_INVALID_ARG, "block must be 64, 128 or 256");
   if (launch->order > MC_ORDER_GIVEN) return bfail(b, MC_ERR_INVALID_ARG, "unknown queue order");
-  if (b->graph_launches) {  // the graph in flight reads the parameter table
+  if (b->iterations) {  // the iteration in flight reads the parameter table
     const cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "set launch");
   }
@@ -307,6 +317,17 @@ mc_status mc_batch_set_launch(mc_batch *b, const mc_batch_launch *launch) {
   b->bps_req = launch->blocks_per_sm;
   b->order_policy = launch->order;
   b->grid = b->nsm * resolved_bps(b);
+  drop_graph(b);
+  return MC_OK;
+}
+
+mc_status mc_batch_capture_graph(mc_batch *b, int32_t enable) {
+  if (!b || (enable != 0 && enable != 1)) return MC_ERR_INVALID_ARG;
+  if (b->iterations) {  // the iteration in flight may still be the graph
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "capture graph");
+  }
+  b->use_graph = enable == 1;
   drop_graph(b);
   return MC_OK;
 }

@@ -44,7 +44,7 @@ EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_run_iter
             "mc_status_string", "mc_last_error_message", "mc_transport_noalloc",
             "mc_batch_create", "mc_batch_run_iteration", "mc_batch_synchronize",
             "mc_batch_read_timing", "mc_batch_last_error_message", "mc_batch_destroy",
-            "mc_batch_set_launch", "mc_batch_get_launch", "mc_batch_autotune",
+            "mc_batch_set_launch", "mc_batch_get_launch", "mc_batch_autotune", "mc_batch_capture_graph",
             "mc_device_estimators", "mc_set_virtual_packets", "mc_read_virtual_spectrum",
             "mc_t_inner_from_luminosity", "mc_emitted_luminosity", "mc_t_inner_update")
 
@@ -219,6 +219,8 @@ def load(build_if_missing: bool = True):
     L.mc_batch_set_launch.argtypes = [vp, P(mc_batch_launch)]
     L.mc_batch_get_launch.restype = i32
     L.mc_batch_get_launch.argtypes = [vp, P(mc_batch_launch)]
+    L.mc_batch_capture_graph.restype = i32
+    L.mc_batch_capture_graph.argtypes = [vp, i32]
     L.mc_batch_autotune.restype = i32
     L.mc_batch_autotune.argtypes = [vp, vp, vp, vp, vp, P(mc_batch_launch), vp, vp]
     _lib = L
@@ -591,6 +593,11 @@ class Batch:
     def set_launch(self, block=0, blocks_per_sm=0, order=MC_ORDER_PACKETS):
         c = mc_batch_launch(block, blocks_per_sm, order)
         return self._bcheck(load().mc_batch_set_launch(self.h, C.byref(c)))
+
+    def capture_graph(self, enable=True):
+        """mc_batch_capture_graph: replay a captured CUDA graph (default) or
+        enqueue the kernels directly every iteration."""
+        return self._bcheck(load().mc_batch_capture_graph(self.h, int(bool(enable))))
 
     def launch(self):
         c = mc_batch_launch()

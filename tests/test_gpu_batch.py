@@ -101,13 +101,15 @@ def test_launch_shape_and_autotune_leave_results_unchanged(mc):
     """Block size, resident blocks per SM and queue order change only which
     thread carries a packet and when; J, nu_bar, T_R, W stay bit-identical and
     the packets' fates and frequencies identical.  The autotuner's trials
-    (transport only) leave the models' state as it was."""
+    (transport only) leave the models' state as it was, and so does running
+    the iteration as plain launches instead of a graph replay."""
     specs = _specs()
     seeds = [7 + k for k in range(len(specs))]
     n = [s.n_packets for s in specs]
     t_in = [s.t_inner for s in specs]
     shapes = [None, dict(block=64, blocks_per_sm=1, order=mc.MC_ORDER_GIVEN),
-              dict(block=256, blocks_per_sm=0, order=mc.MC_ORDER_WORK), "autotune"]
+              dict(block=256, blocks_per_sm=0, order=mc.MC_ORDER_WORK), "autotune",
+              "direct", "graph_then_direct"]
     results = []
     for shape in shapes:
         models = [mc.Model(s, precision=mc.MC_PRECISION_MIXED, record_packets=True) for s in specs]
@@ -118,12 +120,16 @@ def test_launch_shape_and_autotune_leave_results_unchanged(mc):
             best, ms, trials = b.autotune(seeds, 0, n, t_in)
             assert best["block"] in (64, 128, 256) and best["blocks_per_sm"] >= 1 and ms > 0 and trials >= 4
             assert b.launch() == best
-        elif shape is not None:
+        elif shape == "direct":
+            b.capture_graph(False)  # plain launches every iteration
+        elif shape is not None and shape != "graph_then_direct":
             b.set_launch(**shape)
             got = b.launch()
             assert got["block"] == shape["block"] and got["order"] == shape["order"]
         out = []
         for it in range(2):
+            if shape == "graph_then_direct" and it == 1:
+                b.capture_graph(False)
             b.run_iteration(seeds, it, n, t_in, update=True)
             b.synchronize()
             per = []
@@ -155,5 +161,6 @@ def test_set_launch_rejects_unknown_shapes(mc):
         b.set_launch(order=9)
     b.set_launch(block=256, blocks_per_sm=1000)  # clamped to what fits
     assert 1 <= b.launch()["blocks_per_sm"] <= 8
+    assert mc.load().mc_batch_capture_graph(b.h, 2) == mc.MC_ERR_INVALID_ARG
     b.close()
     m.close()

@@ -1,0 +1,73 @@
+"""Resuming the iteration cycle from a saved state on the GPU (Sect. 2.8).
+
+The cycle's state is T_R and W per shell (read with mc_read_plasma, restored
+with mc_set_plasma); everything else is keyed by (seed, iteration, packet).
+A fresh model restored from the state after iteration 1 and run from
+iteration 2 must reproduce the uninterrupted run: in mixed precision bit for
+bit (fixed-point J, nu_bar make T_R, W independent of summation order), in
+binary64 to the estimators' summation order (per-packet fates, nu, E and
+counters equal; J, nu_bar, T_R, W within 1e-12).
+"""
+import numpy as np
+import pytest
+
+from paper_1401_5469_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1401_5469_gb300 import mc as mcmod
+    mcmod.load()
+    return mcmod
+
+
+def _iterate(mc, spec, precision, iterations, state=None):
+    n = spec.n_packets
+    m = mc.Model(spec, precision=precision, record_packets=True, max_packets=n, j_blue=False)
+    if state is None:
+        m.set_plasma()
+    else:
+        m.set_plasma(t_rad=state[0], w=state[1])
+    out = []
+    for it in iterations:
+        m.run_iteration(5469, it, n, spec.t_inner)
+        pk = m.packets(0, n)
+        j, nb, _, _ = m.estimators()
+        t, w = m.update_radiation_field()
+        out.append((pk, j, nb, t, w))
+    t, w, _ = m.plasma()
+    m.close()
+    return out, (t, w)
+
+
+@pytest.mark.parametrize("kind", ["downbranch", "nebular"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_resume_from_saved_state(mc, kind, precision):
+    if kind == "downbranch":
+        spec = synth.downbranch_model(n_lines=20000, n_shells=12, n_packets=4000, seed=31)
+    else:
+        spec = synth.nebular_model(mode=2, n_lines=20000, n_shells=12, n_packets=4000, seed=32)
+    full, _ = _iterate(mc, spec, precision, range(4))
+    _, state = _iterate(mc, spec, precision, range(2))
+    tail, _ = _iterate(mc, spec, precision, range(2, 4), state)
+    exact = precision == mc.MC_PRECISION_MIXED
+    for (pa, ja, na, ta, wa), (pb, jb, nb, tb, wb) in zip(full[2:], tail):
+        st_a, st_b = pa[0], pb[0]
+        if exact:
+            for a, b in zip(pa, pb):
+                np.testing.assert_array_equal(a, b)
+            for a, b in ((ja, jb), (na, nb), (ta, tb), (wa, wb)):
+                np.testing.assert_array_equal(a, b)
+        else:
+            agree = st_a == st_b
+            assert (~agree).sum() <= int(1e-5 * st_a.size)
+            for a, b in zip(pa[1:3], pb[1:3]):
+                np.testing.assert_allclose(a[agree], b[agree], rtol=1e-12)
+            assert np.array_equal(pa[3][agree], pb[3][agree])
+            for a, b in ((ja, jb), (na, nb), (ta, tb), (wa, wb)):
+                np.testing.assert_allclose(a, b, rtol=1e-12)
