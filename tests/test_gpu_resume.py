@@ -5,8 +5,10 @@ with mc_set_plasma); everything else is keyed by (seed, iteration, packet).
 A fresh model restored from the state after iteration 1 and run from
 iteration 2 must reproduce the uninterrupted run: in mixed precision bit for
 bit (fixed-point J, nu_bar make T_R, W independent of summation order), in
-binary64 to the estimators' summation order (per-packet fates, nu, E and
-counters equal; J, nu_bar, T_R, W within 1e-12).
+binary64 to the estimators' summation order (per-packet fates and counters
+equal, nu, E within 1e-12; J, nu_bar, T_R, W within the estimator tolerance
+1e-9: the atomic sums of two runs differ by up to ~2e-12 after a few
+iterations).
 """
 import numpy as np
 import pytest
@@ -70,4 +72,4 @@ def test_resume_from_saved_state(mc, kind, precision):
                 np.testing.assert_allclose(a[agree], b[agree], rtol=1e-12)
             assert np.array_equal(pa[3][agree], pb[3][agree])
             for a, b in ((ja, jb), (na, nb), (ta, tb), (wa, wb)):
-                np.testing.assert_allclose(a, b, rtol=1e-12)
+                np.testing.assert_allclose(a, b, rtol=1e-9)
