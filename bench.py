@@ -72,13 +72,41 @@ TRAFFIC_CAPTURE = {
 }
 
 
-def _captured_traffic():
+# Binary64 lane operations (DADD + DMUL + DFMA thread instructions) per
+# flight segment of the same kernel, from ncu's sass_thread_inst_executed
+# counters on the 1e5-packet case of this model (profiles/
+# transport_fp64_downbranch_1e5_fp64_ops.md); null for other sources.
+FP64_OPS_CAPTURE = {
+    "lane_ops_per_segment": 76.66,
+    "sources": TRAFFIC_CAPTURE["sources"],
+    "sha256": TRAFFIC_CAPTURE["sha256"],
+}
+# Binary64 peak of the FP64 pipes: 2 lane operations per SM per cycle (ncu's
+# peak_sustained for DFMA) x 152 SMs at the 2070 MHz maximum SM clock.
+FP64_PEAK_OPS = 2 * 152 * 2.070e9
+
+
+def _sources_match(capture):
     import hashlib
     h = hashlib.sha256()
-    for rel in TRAFFIC_CAPTURE["sources"]:
+    for rel in capture["sources"]:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
-    return TRAFFIC_CAPTURE["dram_bytes_per_launch"] if h.hexdigest() == TRAFFIC_CAPTURE["sha256"] else None
+    return h.hexdigest() == capture["sha256"]
+
+
+def _captured_traffic():
+    return TRAFFIC_CAPTURE["dram_bytes_per_launch"] if _sources_match(TRAFFIC_CAPTURE) else None
+
+
+def _fp64_roofline(segments, seconds):
+    ops = FP64_OPS_CAPTURE["lane_ops_per_segment"]
+    if ops is None or not _sources_match(FP64_OPS_CAPTURE):
+        return None
+    achieved = ops * segments / seconds
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9, "unit": "G lane-ops/s",
+            "frac": achieved / FP64_PEAK_OPS, "lane_ops_per_segment": ops, "kernel": "transport_fp64",
+            "peak_kind": "derived: 2 binary64 lanes/SM/cycle x 152 SMs x 2070 MHz"}
 
 
 def _peaks():
@@ -358,6 +386,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _captured_traffic(), "kernel": "transport_fp64",
                      "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes},
+        "roofline_fp64": _fp64_roofline(per["segments"], k1_ms * 1e-3),
         "cpu_baseline": cpu,
         "e2e": {"value": ws * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
