@@ -64,7 +64,10 @@ typedef int32_t mc_status;
 /* Precision modes. */
 #define MC_PRECISION_FP64 0  /* all transport arithmetic in binary64 */
 #define MC_PRECISION_MIXED 1 /* distances and optical depths in binary32; comoving
-                                frequency, line-resonance test and estimators in binary64 */
+                                frequency and line-resonance test in binary64; J, nu_bar
+                                and J_blue summed exactly in 64-bit fixed point from
+                                binary32 contributions (line frequencies must lie in
+                                (1e-30, 1e30) Hz) */
 
 /* Packet fates reported by mc_read_packets. */
 #define MC_PACKET_ESCAPED 1
@@ -357,11 +360,10 @@ void mc_model_destroy(mc_model *m);
  * Monte Carlo iteration each with a single persistent transport launch: the
  * packets of all models are drawn from one queue (largest model first by
  * default).  Each model's iteration is exactly its single-model iteration:
- * the same draws, the same compiled kernel, and J and nu_bar summed in fixed
- * point, so J, nu_bar and the updated T_R, W are bit-identical to the model
- * run alone; only the binary64 J_blue and spectrum sums depend on summation
- * order.  The whole
- * iteration -- Sobolev depths where stale, estimator zeroing, transport and,
+ * the same draws, the same compiled kernel, and J, nu_bar and J_blue summed
+ * in fixed point, so they and the updated T_R, W are bit-identical to the
+ * model run alone; only the binary64 spectrum sums depend on summation order.
+ * The whole iteration -- Sobolev depths where stale, estimator zeroing, transport and,
  * when `update` is set, Eqs. 15-16 for every model -- is captured as one CUDA
  * graph on the first call and replayed while the batch's shape (models with
  * stale depths, update flag, total packets) is unchanged.  Results are read

@@ -312,8 +312,14 @@ def run_iteration(om: OracleModel, seed: int, iteration: int, n_packets: int, t_
     res = _Result(j_est=_p(r.j_est), nu_bar=_p(r.nu_bar), j_blue=_p(r.j_blue),
                   spectrum=_p(r.spectrum), status=_p(r.status), nu_out=_p(r.nu),
                   e_out=_p(r.energy), counters=_p(r.counters), spectrum_v=_p(r.spectrum_v))
-    rc = lib().orc_run(C.byref(om.c), seed, iteration, n_packets, float(t_inner), first, count,
-                       threads, C.byref(res))
+    # the model's flag switches the accumulation on; j_blue= overrides it for this call
+    saved = om.c.j_blue
+    om.c.j_blue = int(bool(want_jb))
+    try:
+        rc = lib().orc_run(C.byref(om.c), seed, iteration, n_packets, float(t_inner), first, count,
+                           threads, C.byref(res))
+    finally:
+        om.c.j_blue = saved
     if rc != 0:
         raise ValueError(f"oracle rejected the model (rc={rc})")
     r.stats = dict(zip(STAT_NAMES, [int(v) for v in res.stats]))

@@ -178,6 +178,8 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
     if (j > 0 && !(lines->nu[j] < lines->nu[j - 1]))
       return fail(nullptr, MC_ERR_INVALID_ARG, "line frequencies must be strictly descending");
   }
+  if (run->precision == MC_PRECISION_MIXED && !(lines->nu[0] < 1e30 && lines->nu[L - 1] > 1e-30))
+    return fail(nullptr, MC_ERR_INVALID_ARG, "mixed precision needs line frequencies in (1e-30, 1e30) Hz");
   if (run->line_mode != MC_LINE_SCATTER && run->line_mode != MC_LINE_DOWNBRANCH &&
       run->line_mode != MC_LINE_MACROATOM)
     return fail(nullptr, MC_ERR_INVALID_ARG, "unknown line_mode");
@@ -657,10 +659,15 @@ mc_status model_prepare(mc_model *m, cudaStream_t st, bool events) {
 
 mc_status model_finish_transport(mc_model *m, const TransportParams &p, cudaStream_t st) {
   if (!m->est_fix) return MC_OK;
-  const cudaError_t e = launch_est_from_fix(m->est_fix, static_cast<int>(m->S), p.e_cmf, p.nu_scale,
-                                            m->j_est, m->nu_bar, st);
+  cudaError_t e = launch_est_from_fix(m->est_fix, static_cast<int>(m->S), p.e_cmf, p.nu_scale,
+                                      m->j_est, m->nu_bar, st);
   if (e != cudaSuccess) return cuda_fail(m, e, "estimator conversion");
   m->launches += 1;
+  if (m->j_blue) {
+    e = launch_jblue_from_fix(m->j_blue, static_cast<size_t>(m->S) * m->L, p.e_cmf, p.inv_nu_ref, st);
+    if (e != cudaSuccess) return cuda_fail(m, e, "J_blue conversion");
+    m->launches += 1;
+  }
   return MC_OK;
 }
 

@@ -179,6 +179,9 @@ cudaError_t launch_transport_batch(const TransportParams &p, int line_mode, bool
 size_t mixed_smem_bytes(int S);
 cudaError_t launch_to_f32(const double *in, float *out, size_t n, cudaStream_t st);
 // j_est = fix[s] 2^-32 E, nu_bar = fix[S + s] 2^-32 E nu_ref (mixed precision).
+// J_blue of a mixed launch is summed in the j_blue buffer as 64-bit fixed
+// point (units of 2^-32 E / nu_ref) and converted in place after the launch.
+cudaError_t launch_jblue_from_fix(double *j_blue, size_t n, double e_cmf, double inv_nu_ref, cudaStream_t st);
 cudaError_t launch_est_from_fix(const unsigned long long *fix, int S, double e_cmf, double nu_ref,
                                 double *j_est, double *nu_bar, cudaStream_t st);
 cudaError_t launch_ionization(const IonParams &p, cudaStream_t st);  // two kernels

@@ -273,6 +273,16 @@ __global__ void row_info_kernel(uint32_t L, const int32_t *line_row, const uint3
   row_info[j] = b | (n << 32);
 }
 
+// J_blue of a mixed-precision launch, in place: the buffer holds 64-bit
+// fixed-point sums in units of 2^-32 E / nu_ref; overwrite each with
+// sum 2^-32 E / nu_ref (E the packet energy).
+__global__ void jblue_from_fix_kernel(double *jb, size_t n, double e_cmf, double inv_nu_ref) {
+  unsigned long long *fix = reinterpret_cast<unsigned long long *>(jb);
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n; i += stride)
+    jb[i] = ((static_cast<double>(fix[i]) * (1.0 / kEstFixScale)) * e_cmf) * inv_nu_ref;
+}
+
 __global__ void est_from_fix_kernel(const unsigned long long *fix, int S, double e_cmf, double nu_ref,
                                     double *j_est, double *nu_bar) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -360,6 +370,11 @@ cudaError_t launch_dbr_setup(uint32_t nnz, uint32_t n_rows, uint32_t L, int K,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   row_info_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, line_row, dbr_offset, row_info);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jblue_from_fix(double *j_blue, size_t n, double e_cmf, double inv_nu_ref, cudaStream_t st) {
+  jblue_from_fix_kernel<<<4 * 152, 256, 0, st>>>(j_blue, n, e_cmf, inv_nu_ref);
   return cudaGetLastError();
 }
 

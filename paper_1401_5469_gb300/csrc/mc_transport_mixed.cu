@@ -51,7 +51,8 @@ struct MCtx {
   double *j_blue, *j_est, *nu_bar, *spectrum;
   unsigned long long *stats;
   unsigned long long *est_fix;  // [2 S] J, nu_bar in fixed point
-  float inv_nu_ref;
+  unsigned long long *jb_fix;   // [S L] J_blue in fixed point (the j_blue buffer, converted after the launch)
+  float inv_nu_ref, nu_ref;
   const double *planck;
   int32_t S, L, spec_bins;
   uint32_t key0, key1, iteration;
@@ -81,7 +82,9 @@ __device__ __forceinline__ void load_ctx(MCtx &c, const TransportParams &q, cons
   c.spectrum = q.spectrum;
   c.stats = q.stats;
   c.est_fix = q.est_fix;
+  c.jb_fix = reinterpret_cast<unsigned long long *>(q.j_blue);
   c.inv_nu_ref = static_cast<float>(q.inv_nu_ref);
+  c.nu_ref = static_cast<float>(q.nu_scale);
   c.planck = q.planck_cdf;
   c.spec_bins = q.spec_bins;
   c.key0 = q.key0;
@@ -135,6 +138,16 @@ __device__ __forceinline__ void pick_m(const MCtx &c, unsigned long long rinfo, 
 }
 
 __device__ __forceinline__ float max0f(float v) { return v > 0.0f ? v : 0.0f; }
+
+// binary32 value of a positive binary64 (given as its bit pattern) inside
+// binary32's normal range, rounded toward zero, with integer operations only
+// (the line frequencies are validated to lie in that range).
+__device__ __forceinline__ float f32_of_positive_f64(long long bits) {
+  const unsigned long long b = static_cast<unsigned long long>(bits);
+  const uint32_t e = static_cast<uint32_t>(b >> 52) - 1023u + 127u;
+  const uint32_t m = static_cast<uint32_t>(b >> 29) & 0x7fffffu;
+  return __uint_as_float((e << 23) | m);
+}
 
 // x mu at the shell exit, +sqrt(x_out^2 - q) or -sqrt(x_in^2 - q).
 __device__ __forceinline__ float shell_exit_f(float q, bool inner, float xi2, float xo2) {
@@ -312,7 +325,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
         key_e = rawkey(thr_e);  // compared only with positive keys
       }
       long long key_thr = key_e;
-      const float e_inv2 = JB ? (pk.e_lab * inv_nu) * inv_nu : 0.0f;
+      // J_blue contribution E_lab (nu_j / nu_lab)^2 / nu_j = (nu_j / nu_lab) E_lab / nu_lab,
+      // in units of E / nu_ref and 2^-32 (fixed point, like J and nu_bar)
+      const float e_jb = JB ? ((pk.e_lab * inv_nu) * c.nu_ref) * kEstFixScaleF : 0.0f;
       const size_t row = static_cast<size_t>(s) * static_cast<size_t>(L);
       const float *tau_s = c.tau32 + row;
       const long long *nub = reinterpret_cast<const long long *>(c.nu);
@@ -363,7 +378,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
             if (bj <= key_shell) break;  // this line lies beyond the exit
           }
           pk.cnt[2] += 1u;
-          if (JB) atomicAdd(c.j_blue + row + j, static_cast<double>(static_cast<float>(nuj) * e_inv2) * c.e_cmf);
+          if (JB) atomicAdd(c.jb_fix + row + j, __float2ull_rn((f32_of_positive_f64(bj) * inv_nu) * e_jb));
           if (thomson) {
             thr_e = t;
             key_e = rawkey(t);
@@ -375,7 +390,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
           const float lj = max0f(static_cast<float>(nu_cmf - nuj) * inv_nu);
           if (!have_shell && !inside_shell_f(pp, q, lj, inner, xi2, xo2)) break;  // exit comes first
           pk.cnt[2] += 1u;
-          if (JB) atomicAdd(c.j_blue + row + j, static_cast<double>(static_cast<float>(nuj) * e_inv2) * c.e_cmf);
+          if (JB) atomicAdd(c.jb_fix + row + j, __float2ull_rn((f32_of_positive_f64(bj) * inv_nu) * e_jb));
           kind = kLineEvent;
           l = lj;
           nu_hit = nuj;

@@ -68,3 +68,32 @@ def test_mixed_within_monte_carlo_noise(mc, kind):
     r = oracle.run_iteration(om, 5469, 0, n, spec.t_inner, record=False, threads=4)
     norm = oracle.estimator_norm(spec)
     assert np.all(np.abs(r.j_est * norm - j32)[keep] <= 5 * sJ[keep] + 1e-12 * np.abs(j64[keep]))
+
+
+def test_mixed_j_blue_fixed_point_in_transparent_ejecta(mc):
+    """Transparent ejecta: every packet flies one straight path past the same
+    Sobolev points in both precisions, so the mixed-precision J_blue (binary32
+    contributions summed in 64-bit fixed point) differs from the oracle's
+    binary64 sums only by those roundings: within 1e-5 per (shell, line) cell
+    with at least ~10 passes, and within 1e-6 summed over shells per line."""
+    spec = synth.free_streaming_model(n_shells=8, n_lines=400, n_packets=40000)
+    m = mc.Model(spec, precision=mc.MC_PRECISION_MIXED, j_blue=True)
+    m.set_plasma(tau=spec.tau)
+    m.run_iteration(11, 0, spec.n_packets, spec.t_inner)
+    _, _, jb, _ = m.estimators(j_blue=True)
+    _, stats, _ = m.spectrum()
+    m.close()
+    om = oracle.OracleModel(spec, tau=spec.tau)
+    r = oracle.run_iteration(om, 11, 0, spec.n_packets, spec.t_inner, threads=4, record=False,
+                             j_blue=True)
+    ref = r.j_blue.reshape(spec.n_shells, spec.n_lines)
+    # a packet passes the lines within the ~7% Doppler sweep below its frequency
+    assert abs(stats["resonances"] - r.stats["resonances"]) <= 2 and r.stats["resonances"] > 2 * spec.n_packets
+    per_pass = ref.sum() / r.stats["resonances"]
+    busy = ref > 10 * per_pass
+    assert busy.sum() > 1000
+    # a Sobolev point within binary32 rounding of a shell boundary may be
+    # counted in the neighbouring shell: allow two such cells
+    off = np.abs(jb[busy] - ref[busy]) > 1e-5 * ref[busy]
+    assert off.sum() <= 2, off.sum()
+    np.testing.assert_allclose(jb.sum(axis=0), ref.sum(axis=0), rtol=1e-6)
