@@ -20,6 +20,11 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libmc_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The mixed-precision kernel is compiled twice with different register caps
+# (single models, batches) and must compute the same bits in both: only its
+# explicit fma/fmaf calls fuse, so no multiply-add contraction can depend on
+# how the registers were allocated.
+PER_FILE_FLAGS = {"mc_transport_mixed.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -57,7 +62,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc] + flags + ["-c", src, "-o", obj]
+        cmd = [cc] + flags + PER_FILE_FLAGS.get(os.path.basename(src), []) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -204,11 +204,15 @@ __device__ __forceinline__ void flush_stats(Stats &st, unsigned long long *dst) 
   }
 }
 
-// One kernel serves a single model (p.n_models == 0) and a batch: the two
-// launches run the same machine code, so a model's results do not depend on
-// the company it is launched in.
-template <int MODE, bool JB, bool REC>
-__global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportParams p) {
+// One kernel source serves a single model (p.n_models == 0) and a batch, so a
+// model's results do not depend on the company it is launched in.  It is
+// compiled twice, differing only in register allocation: MINB = 1 (up to 255
+// registers: the shortest chain for a single model's last random walks) for
+// single models, MINB = 2 (128 registers: 16 resident warps per SM instead of
+// 12) for batches, whose throughput phase dominates.  The arithmetic is the
+// same instruction for instruction; the batch tests check the bits.
+template <int MODE, bool JB, bool REC, int MINB>
+__global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const TransportParams p) {
   extern __shared__ unsigned long long smem_u64[];
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lanemask_lt = (1u << lane) - 1u;
@@ -541,23 +545,26 @@ __global__ void __launch_bounds__(kMaxBlock, 1) transport_mixed(const TransportP
   if (lane == 0u) atomicMax(p.flags + 2, global_ns());
 }
 
-template <int MODE, bool JB, bool REC>
+template <int MODE, bool JB, bool REC, int MINB>
 const void *kptr() {
-  return reinterpret_cast<const void *>(&transport_mixed<MODE, JB, REC>);
+  return reinterpret_cast<const void *>(&transport_mixed<MODE, JB, REC, MINB>);
 }
 
-const void *select_b(int line_mode, bool jb, bool rec) {
+template <int MINB>
+const void *select_m(int line_mode, bool jb, bool rec) {
   if (line_mode == 0) {
-    if (jb) return rec ? kptr<0, true, true>() : kptr<0, true, false>();
-    return rec ? kptr<0, false, true>() : kptr<0, false, false>();
+    if (jb) return rec ? kptr<0, true, true, MINB>() : kptr<0, true, false, MINB>();
+    return rec ? kptr<0, false, true, MINB>() : kptr<0, false, false, MINB>();
   }
-  if (jb) return rec ? kptr<1, true, true>() : kptr<1, true, false>();
-  return rec ? kptr<1, false, true>() : kptr<1, false, false>();
+  if (jb) return rec ? kptr<1, true, true, MINB>() : kptr<1, true, false, MINB>();
+  return rec ? kptr<1, false, true, MINB>() : kptr<1, false, false, MINB>();
 }
+
+const void *select_b(int line_mode, bool jb, bool rec) { return select_m<2>(line_mode, jb, rec); }
 
 }  // namespace
 
-const void *select_mixed_kernel(int line_mode, bool jb, bool rec) { return select_b(line_mode, jb, rec); }
+const void *select_mixed_kernel(int line_mode, bool jb, bool rec) { return select_m<1>(line_mode, jb, rec); }
 
 size_t mixed_smem_bytes(int S) { return 4 * static_cast<size_t>(S) * sizeof(float); }
 
