@@ -336,6 +336,9 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
 
   auto bail = [&](mc_status code, const std::string &msg) {
     g_create_error = msg;
+    // copies already enqueued must finish before a caller's allocator gets
+    // its blocks back (the default stream-ordered free needs no wait)
+    cudaStreamSynchronize(m->stream);
     free_all(m);
     cudaStreamSynchronize(m->stream);
     for (int i = 0; i < kNEv; ++i) cudaEventDestroy(m->ev[i]);

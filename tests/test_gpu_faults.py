@@ -1,0 +1,104 @@
+"""Host-side failure injection on a GPU machine (no device fault is provoked).
+
+* a caller-supplied allocator that fails at the k-th request: model creation
+  returns MC_ERR_OOM with a message, and every block it had obtained is
+  handed back through the allocator's free;
+* after a successful create, run and destroy, the allocator holds nothing;
+* the transport deadline: covered by tests/test_gpu_parity.py.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_1401_5469_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1401_5469_gb300 import mc as mcmod
+    mcmod.load()
+    return torch, mcmod
+
+
+def _descs(mc, spec, keep):
+    f64 = lambda a: keep.append(np.ascontiguousarray(a, np.float64)) or keep[-1].ctypes.data
+    i32 = lambda a: keep.append(np.ascontiguousarray(a, np.int32)) or keep[-1].ctypes.data
+    g = mc.mc_geometry_desc(n_shells=spec.n_shells, v_inner=f64(spec.v_inner), v_outer=f64(spec.v_outer),
+                            n_e=f64(spec.n_e), t_exp=spec.t_exp)
+    l = mc.mc_line_desc(n_lines=spec.n_lines, nu=f64(spec.nu), f=f64(spec.f), ion=i32(spec.ion),
+                        lower=i32(spec.lower), upper=i32(spec.upper))
+    a = mc.atomic_desc(spec, keep)
+    r = mc.mc_run_desc(line_mode=int(spec.line_mode), precision=0, j_blue=1, record_packets=1,
+                       spec_bins=100, spec_nu_lo=1e14, spec_nu_hi=3e15, max_packets=spec.n_packets,
+                       max_segments=0, delta_t=1.0)
+    return g, l, a, r
+
+
+class _Allocator:
+    """Device blocks from torch; the k-th request fails."""
+
+    def __init__(self, torch, mc, fail_at=None):
+        self.live, self.calls, self.fail_at = {}, 0, fail_at
+
+        def alloc(nbytes, ctx):
+            self.calls += 1
+            if self.calls == self.fail_at:
+                return None
+            t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device="cuda")
+            self.live[t.data_ptr()] = t
+            return t.data_ptr()
+
+        def free(ptr, ctx):
+            self.live.pop(ptr)
+
+        self._a, self._f = mc.ALLOC_FN(alloc), mc.FREE_FN(free)
+        self.c = mc.mc_allocator(alloc=self._a, free=self._f, ctx=None)
+
+
+def test_allocation_failure_is_reported_and_released(env):
+    torch, mc = env
+    spec = synth.downbranch_model(n_lines=2000, n_shells=6, n_packets=200)
+    keep = []
+    g, l, a, r = _descs(mc, spec, keep)
+    L = mc.load()
+    total = _Allocator(torch, mc)
+    h = C.c_void_p()
+    assert L.mc_model_create(C.byref(g), C.byref(l), C.byref(a), C.byref(r), C.byref(total.c), None,
+                             C.byref(h)) == 0
+    L.mc_model_destroy(h)
+    torch.cuda.synchronize()
+    assert total.calls > 10 and not total.live
+    for k in (1, 2, total.calls // 2, total.calls):
+        al = _Allocator(torch, mc, fail_at=k)
+        h = C.c_void_p()
+        rc = L.mc_model_create(C.byref(g), C.byref(l), C.byref(a), C.byref(r), C.byref(al.c), None,
+                               C.byref(h))
+        torch.cuda.synchronize()
+        assert rc == mc.MC_ERR_OOM, (k, rc)
+        assert not h.value
+        assert "allocation" in L.mc_last_error_message(None).decode()
+        assert not al.live, (k, len(al.live))
+
+
+def test_run_and_destroy_release_everything(env):
+    torch, mc = env
+    spec = synth.downbranch_model(n_lines=2000, n_shells=6, n_packets=200)
+    keep = []
+    g, l, a, r = _descs(mc, spec, keep)
+    L = mc.load()
+    al = _Allocator(torch, mc)
+    h = C.c_void_p()
+    assert L.mc_model_create(C.byref(g), C.byref(l), C.byref(a), C.byref(r), C.byref(al.c), None,
+                             C.byref(h)) == 0
+    assert L.mc_set_plasma(h, None, None, None) == 0
+    assert L.mc_run_iteration(h, 5, 0, spec.n_packets, spec.t_inner) == 0
+    assert L.mc_synchronize(h) == 0
+    L.mc_model_destroy(h)
+    torch.cuda.synchronize()
+    assert al.calls > 10 and not al.live
