@@ -65,10 +65,10 @@ L2_BYTES = 129 * 2**20
 # kernel built from these sources only: with any other source hash the
 # bench reports traffic as null.
 TRAFFIC_CAPTURE = {
-    "dram_bytes_per_launch": 622.74e6 + 111.90e6,
+    "dram_bytes_per_launch": 627.22e6 + 112.87e6,
     "sources": ("paper_1401_5469_gb300/csrc/mc_transport.cu", "paper_1401_5469_gb300/csrc/mc_device.cuh",
                 "paper_1401_5469_gb300/csrc/mc_internal.h"),
-    "sha256": "6cb644c1fd3fddd05e1cd5ef08f2d044731ba2c1f5b6b824aff26ea9f88302ae",
+    "sha256": "878beff05520587e3e52ea28151f1fa73bdd6bedbe49bdae2963024179cb7656",
 }
 
 
@@ -77,7 +77,7 @@ TRAFFIC_CAPTURE = {
 # counters on the 1e5-packet case of this model (profiles/
 # transport_fp64_downbranch_1e5_fp64_ops.md); null for other sources.
 FP64_OPS_CAPTURE = {
-    "lane_ops_per_segment": 76.66,
+    "lane_ops_per_segment": 76.73,
     "sources": TRAFFIC_CAPTURE["sources"],
     "sha256": TRAFFIC_CAPTURE["sha256"],
 }
