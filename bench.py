@@ -41,6 +41,7 @@ end, with the backlog left at the end reported beside them.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -452,45 +453,66 @@ def run_batched(args):
     total_packets = int(sum(n))
     stream = torch.cuda.current_stream()
 
-    # ---- batched, mixed precision
+    # ---- batched, mixed precision: G groups of models, one batch (persistent
+    # launch, own stream) each; a group's next iteration is enqueued as soon as
+    # its last one ends, so one group's bulk fills the SMs another's tail of
+    # long random walks leaves idle (a model's results do not depend on its group)
     jb = bool(args.j_blue)
+    G = max(1, min(args.groups, n_models))
     t0 = time.perf_counter()
-    models = [mc.Model(s, precision=mc.MC_PRECISION_MIXED, j_blue=jb) for s in specs]
+    # deal models by work (packets x lines) round-robin, so the groups balance;
+    # a group's models share one stream (the batch orders itself after it)
+    by_work = sorted(range(n_models), key=lambda k: -n[k] * specs[k].n_lines)
+    groups = [by_work[g::G] for g in range(G)]
+    g_streams = [torch.cuda.Stream() for _ in range(G)]
+    group_of = {k: g for g, grp in enumerate(groups) for k in grp}
+    models = [mc.Model(s, precision=mc.MC_PRECISION_MIXED, j_blue=jb,
+                       stream=ctypes.c_void_p(g_streams[group_of[k]].cuda_stream))
+              for k, s in enumerate(specs)]
     for m in models:
         m.set_plasma()
-    b = mc.Batch(models)
+    batches = [mc.Batch([models[k] for k in grp]) for grp in groups]
+    gargs = [([seeds[k] for k in grp], [n[k] for k in grp], [t_in[k] for k in grp]) for grp in groups]
     torch.cuda.synchronize()
-    _log(f"created mixed models in {time.perf_counter() - t0:.1f} s")
+    _log(f"created mixed models in {time.perf_counter() - t0:.1f} s ({G} groups)")
     t0 = time.perf_counter()
-    tuned, tuned_ms, trials = b.autotune(seeds, 0, n, t_in)
+    tuned, tuned_ms, trials = [], [], 0
+    for b, (sd, np_, ti) in zip(batches, gargs):
+        l_, ms_, tr_ = b.autotune(sd, 0, np_, ti)
+        tuned.append(l_)
+        tuned_ms.append(ms_)
+        trials += tr_
     tune_s = time.perf_counter() - t0
-    _log(f"autotune {tuned} {tuned_ms:.1f} ms after {trials} trials ({tune_s:.1f} s)")
+    _log(f"autotune {tuned} {tuned_ms} ms after {trials} trials ({tune_s:.1f} s)")
     clocks = ClockSampler(0)
     clocks.start()
     torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     transport_ms = []
     work = {"segments": 0, "line_checks": 0, "line_interactions": 0, "e_scatters": 0}
     w0 = time.perf_counter()
-    ev0.record(stream)
+    for b, (sd, np_, ti) in zip(batches, gargs):
+        b.run_iteration(sd, 0, np_, ti, update=True)
     for it in range(n_it):
-        b.run_iteration(seeds, it, n, t_in, update=True)
-        transport_ms.append(b.transport_ms())
-        for m in models:  # per-model run statistics (read after the iteration)
-            st = m.spectrum()[1]
-            for k in work:
-                work[k] += st[k]
-    b.synchronize()
-    ev1.record(stream)
+        for g, (b, (sd, np_, ti)) in enumerate(zip(batches, gargs)):
+            transport_ms.append(b.transport_ms())  # waits for this group's iteration
+            for k in groups[g]:  # per-model run statistics (read after the iteration)
+                st = models[k].spectrum()[1]
+                for key in work:
+                    work[key] += st[key]
+            if it + 1 < n_it:
+                b.run_iteration(sd, it + 1, np_, ti, update=True)
+    for b in batches:
+        b.synchronize()
     torch.cuda.synchronize()
-    wall_b = time.perf_counter() - w0
-    batched_s = ev0.elapsed_time(ev1) / 1e3
+    batched_s = time.perf_counter() - w0
+    wall_b = batched_s
     clk = clocks.stop()
     t_mixed = []
     for m in models:
         t, w, _ = m.plasma()
         t_mixed.append(t)
-    b.close()
+    for b in batches:
+        b.close()
     for m in models:
         m.close()
     _log(f"batched: {batched_s:.2f} s for {n_it} iterations")
@@ -536,12 +558,13 @@ def run_batched(args):
                    "j_blue": jb, "line_mode": "downbranch",
                    "l2": "inputs larger than L2 (Sobolev depths and J_blue of all models)"},
         "packets_per_s": total_packets * n_it / batched_s,
-        "segments_per_s": work["segments"] / (1e-3 * sum(transport_ms)),
-        "line_checks_per_s": work["line_checks"] / (1e-3 * sum(transport_ms)),
+        "segments_per_s": work["segments"] / batched_s,
+        "line_checks_per_s": work["line_checks"] / batched_s,
         "interactions_per_s": (work["line_interactions"] + work["e_scatters"]) / batched_s,
         "segments_per_packet": work["segments"] / (total_packets * n_it),
         "wall_s": wall_b,
-        "transport_ms_per_iteration": transport_ms,
+        "groups": G,
+        "transport_ms_per_group_iteration": transport_ms,
         "autotune": {"launch": tuned, "transport_ms": tuned_ms, "trials": trials, "seconds": tune_s},
         "fp64_per_model": {"models_per_s": fp64_models_s, "seconds": fp64_s, "models_timed": limit,
                            "packets_per_s": sum(n[:limit]) * n_it / fp64_s if limit else None,
@@ -759,6 +782,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="downbranch", choices=["downbranch", "batched", "serve", "spectrum", "macroatom"])
     ap.add_argument("--models", type=int, default=256)
+    ap.add_argument("--groups", type=int, default=2, help="batched workload: model groups on their own streams")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--tick-packets", type=int, default=0)
