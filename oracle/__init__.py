@@ -491,12 +491,16 @@ def plasma_tau(spec, t_rad, w):
 
 
 def run_loop(spec, n_iterations, n_packets, seed, threads=1, t_inner=None, record=False,
-             max_segments=1_000_000, t_rad=None, w=None, first_iteration=0):
+             max_segments=1_000_000, t_rad=None, w=None, first_iteration=0, l_requested=None,
+             t_inner_every=3):
     """The iteration cycle of Sect. 2.8 with T_R = 1e4 K and geometric W to
     start (or the given T_R, W: a run resumed from a saved state), tau
     recomputed from the plasma each iteration and T_R, W updated from the
     estimators after each; iterations are numbered from first_iteration.
-    Returns the per-iteration results."""
+    With l_requested, after every t_inner_every-th iteration T_inner is scaled
+    by (l_requested / L_emitted)^(1/4) (L_emitted from that iteration's
+    escaping packets).  Returns the per-iteration results (r.t_inner: the
+    inner-boundary temperature the iteration ran with)."""
     S = spec.n_shells
     t_in = spec.t_inner if t_inner is None else t_inner
     t_rad = np.full(S, 1.0e4) if t_rad is None else _f64(t_rad).copy()
@@ -516,7 +520,11 @@ def run_loop(spec, n_iterations, n_packets, seed, threads=1, t_inner=None, recor
             om.set_electron_density(n_e)
         r = run_iteration(om, seed, it, n_packets, t_in, threads=threads, record=record)
         r.t_rad_in, r.w_in, r.tau, r.n_e = t_rad.copy(), w.copy(), tau, n_e
+        r.t_inner = t_in
         t_rad, w = update_radiation_field(spec, r.j_est, r.nu_bar, t_rad, w)
         r.t_rad_out, r.w_out = t_rad.copy(), w.copy()
+        r.l_emitted = emitted_luminosity(r.spectrum, om.delta_t)
+        if l_requested is not None and (it - first_iteration + 1) % t_inner_every == 0:
+            t_in = t_inner_update(t_in, l_requested, r.l_emitted)
         out.append(r)
     return out

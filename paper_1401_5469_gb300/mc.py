@@ -485,6 +485,25 @@ class Model:
         _check(load().mc_emitted_luminosity(self.h, C.byref(v)), self.h)
         return v.value
 
+    def iterate(self, seed, n_iterations, n_packets, t_inner, first_iteration=0, l_requested=None,
+                t_inner_every=3, on_iteration=None):
+        """The iteration cycle of Sect. 2.8 through the C ABI: run, update T_R
+        and W (Eqs. 15-16), and with l_requested, after every
+        t_inner_every-th iteration, mc_t_inner_update with this iteration's
+        emitted luminosity.  on_iteration(it, t_inner) is called after each
+        run, before the update.  Returns the T_inner each iteration ran with
+        and the one the next iteration would use."""
+        used = []
+        for it in range(first_iteration, first_iteration + n_iterations):
+            self.run_iteration(seed, it, n_packets, t_inner)
+            used.append(t_inner)
+            if on_iteration is not None:
+                on_iteration(it, t_inner)
+            mc_update_radiation_field(self.h, None, None)
+            if l_requested is not None and (it - first_iteration + 1) % t_inner_every == 0:
+                t_inner = t_inner_update(t_inner, l_requested, self.emitted_luminosity())
+        return used, t_inner
+
     def set_virtual_packets(self, n_virtual: int, tau_v_max: float = 0.0):
         """Virtual packets (Sect. 2.9) in the following iterations (0: off)."""
         return _check(load().mc_set_virtual_packets(self.h, int(n_virtual), float(tau_v_max)), self.h)

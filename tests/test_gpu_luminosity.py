@@ -49,3 +49,34 @@ def test_one_update_reaches_the_requested_luminosity(mc):
     m.run_iteration(5, 0, spec.n_packets, t1)
     assert m.emitted_luminosity() == pytest.approx(l_req, rel=1e-12)
     m.close()
+
+
+def test_luminosity_matching_loop_matches_the_oracle(mc):
+    """Six iterations of the Sect. 2.8 cycle with T_inner matched to a
+    requested luminosity after every third iteration (Model.iterate through
+    the C ABI against oracle.run_loop): the T_inner sequence within 1e-9 (it
+    follows the emitted luminosity, a spectrum sum), and every iteration's
+    packets as in the fixed-T_inner loop parity test."""
+    spec = synth.downbranch_model(n_lines=20000, n_shells=12, n_packets=4000, seed=91, j_blue=False)
+    n = spec.n_packets
+    l_req = 1.3 * oracle.run_loop(spec, 1, n, spec.seed)[0].l_emitted
+    ref = oracle.run_loop(spec, 6, n, spec.seed, record=True, l_requested=l_req)
+    m = mc.Model(spec, record_packets=True, max_packets=n)
+    m.set_plasma()
+    seen = []
+
+    def check(it, t_inner):
+        r = ref[it]
+        st, nu, e, cnt = m.packets(0, n)
+        agree = st == r.status
+        assert (~agree).sum() <= int(1e-5 * n), (it, (~agree).sum())
+        np.testing.assert_allclose(nu[agree], r.nu[agree], rtol=1e-12)
+        np.testing.assert_allclose(e[agree], r.energy[agree], rtol=1e-12)
+        assert np.array_equal(cnt[agree], r.counters[agree])
+        seen.append(t_inner)
+
+    used, _ = m.iterate(spec.seed, 6, n, spec.t_inner, l_requested=l_req, on_iteration=check)
+    m.close()
+    np.testing.assert_allclose(used, [r.t_inner for r in ref], rtol=1e-9)
+    assert used[0] == used[2] and used[3] != used[2] and used[3] == used[5]
+    assert seen == used

@@ -54,3 +54,21 @@ def test_one_update_reaches_the_requested_luminosity_in_free_streaming():
 
 def test_nothing_escaping_keeps_t_inner():
     assert oracle.t_inner_update(9000.0, 1e42, 0.0) == 9000.0
+
+
+def test_luminosity_matching_loop_converges_in_transparent_ejecta():
+    # every third iteration T_inner <- T_inner (L_req / L_emitted)^(1/4); in
+    # transparent ejecta L_emitted scales as T_inner^4, so after the first
+    # update the emitted luminosity sits at L_req within the Monte Carlo noise
+    spec = synth.free_streaming_model(n_packets=20000)
+    t0 = spec.t_inner
+    rs = oracle.run_loop(spec, 6, spec.n_packets, 17, threads=4)
+    l0 = np.array([r.l_emitted for r in rs[:3]])
+    l_req = 0.7 * l0.mean()
+    rl = oracle.run_loop(spec, 6, spec.n_packets, 17, threads=4, l_requested=l_req)
+    t = [r.t_inner for r in rl]
+    assert t[0] == t[1] == t[2] == t0 and t[3] == t[4] == t[5] != t0
+    assert t[3] == pytest.approx(t0 * (l_req / rl[2].l_emitted) ** 0.25, rel=1e-15)
+    sigma = l0.std(ddof=1) * 0.7 + 1e-300
+    for r in rl[3:]:
+        assert abs(r.l_emitted - l_req) < 5 * sigma + 1e-3 * l_req, (r.l_emitted, l_req, sigma)
