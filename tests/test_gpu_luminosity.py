@@ -55,8 +55,9 @@ def test_luminosity_matching_loop_matches_the_oracle(mc):
     """Six iterations of the Sect. 2.8 cycle with T_inner matched to a
     requested luminosity after every third iteration (Model.iterate through
     the C ABI against oracle.run_loop): the T_inner sequence within 1e-9 (it
-    follows the emitted luminosity, a spectrum sum), and every iteration's
-    packets as in the fixed-T_inner loop parity test."""
+    follows the emitted luminosity, a spectrum sum); every iteration's fates
+    and counters agree, final nu and E within 1e-12 in the first iteration
+    and 1e-10 once the carried-over T_R, W differ by rounding."""
     spec = synth.downbranch_model(n_lines=20000, n_shells=12, n_packets=4000, seed=91, j_blue=False)
     n = spec.n_packets
     l_req = 1.3 * oracle.run_loop(spec, 1, n, spec.seed)[0].l_emitted
@@ -70,8 +71,12 @@ def test_luminosity_matching_loop_matches_the_oracle(mc):
         st, nu, e, cnt = m.packets(0, n)
         agree = st == r.status
         assert (~agree).sum() <= int(1e-5 * n), (it, (~agree).sum())
-        np.testing.assert_allclose(nu[agree], r.nu[agree], rtol=1e-12)
-        np.testing.assert_allclose(e[agree], r.energy[agree], rtol=1e-12)
+        # from the second iteration on the two sides run with T_R, W (and
+        # later T_inner) that differ by their estimator sums' rounding
+        # (~1e-13), which the depths carry into every event
+        tol = 1e-12 if it == 0 else 1e-10
+        np.testing.assert_allclose(nu[agree], r.nu[agree], rtol=tol)
+        np.testing.assert_allclose(e[agree], r.energy[agree], rtol=tol)
         assert np.array_equal(cnt[agree], r.counters[agree])
         seen.append(t_inner)
 
