@@ -17,9 +17,10 @@ last random walks overlap the other models' work.
 
 A request's results depend only on its own model, seed and iteration count:
 packet draws are keyed by (seed, iteration, packet), single and batched
-launches run the same kernel, and J, nu_bar are summed in fixed point, so the
-same request gives bit-identical J, nu_bar, T_R and W alone and in any mix
-(only the binary64 J_blue and spectrum sums depend on summation order).
+launches run the same kernel arithmetic, and in mixed precision J, nu_bar and
+J_blue are summed in fixed point, so the same request gives bit-identical J,
+nu_bar, J_blue, T_R and W alone and in any mix (only the spectrum sums, and in
+binary64 the estimator sums, depend on summation order).
 """
 from __future__ import annotations
 
