@@ -54,6 +54,7 @@ def _descs(spec, **run_kw):
     ("bad_mode", mc.MC_ERR_INVALID_ARG),
     ("no_bins", mc.MC_ERR_INVALID_ARG),
     ("downbranch_without_table", mc.MC_ERR_INVALID_ARG),
+    ("too_many_shells", mc.MC_ERR_INVALID_ARG),
 ])
 def test_create_rejects_invalid_models(mutate, expect):
     spec = synth.scatter_model(n_lines=50, n_shells=4)
@@ -65,6 +66,8 @@ def test_create_rejects_invalid_models(mutate, expect):
     elif mutate == "gap":
         spec.v_inner = spec.v_inner.copy()
         spec.v_inner[2] *= 1.01
+    elif mutate == "too_many_shells":
+        spec = synth.scatter_model(n_lines=50, n_shells=1025)
     g, l, r, keep = _descs(spec)
     if mutate == "bad_mode":
         r.line_mode = 7

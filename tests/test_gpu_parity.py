@@ -211,3 +211,24 @@ def test_deadline_returns_timeout_status(mc):
     m2.run_iteration(1, 0, 1000, spec.t_inner)
     m2.estimators()
     m2.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_maximum_shell_count(mc, precision):
+    """1024 shells, the most the shell tables in shared memory hold (the
+    binary64 kernel then needs more than 48 KB of dynamic shared memory):
+    per-packet parity in binary64; in mixed precision every packet finishes
+    and the escaped fraction matches the oracle's within the noise."""
+    spec = synth.scatter_model(n_lines=2000, n_shells=1024, n_packets=2000)
+    n = spec.n_packets
+    m = _run_gpu(mc, spec, spec.tau, n, 21, precision=precision)
+    st, nu, e, cnt = m.packets(0, n)
+    _, stats, _ = m.spectrum()
+    m.close()
+    r = oracle.run_iteration(oracle.OracleModel(spec, tau=spec.tau), 21, 0, n, spec.t_inner, threads=8)
+    assert stats["packets"] == n and stats["shell_crossings"] > 100 * n
+    if precision == 0:
+        assert _compare_packets(st, nu, e, cnt, r).all()
+    else:
+        esc, esc_o = (st == 1).mean(), (r.status == 1).mean()
+        assert abs(esc - esc_o) < 5 * np.sqrt(esc_o * (1 - esc_o) / n) + 1e-3
