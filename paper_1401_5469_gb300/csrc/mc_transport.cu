@@ -608,9 +608,14 @@ int transport_block_size() { return kBlock; }
 
 cudaError_t transport_occupancy(int line_mode, int precision, bool j_blue, bool record, int S,
                                 int *blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, select_kernel(line_mode, precision, j_blue, record), kBlock,
-      smem_bytes(S, precision));
+  const void *k = select_kernel(line_mode, precision, j_blue, record);
+  const size_t smem = smem_bytes(S, precision);
+  if (smem > 48 * 1024) {  // the query, like the launch, needs the opt-in above 48 KB
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kBlock, smem);
 }
 
 cudaError_t launch_transport(const TransportParams &p, int line_mode, int precision, bool j_blue,
