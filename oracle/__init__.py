@@ -27,9 +27,8 @@ Functions and the passage each follows:
                           -- inner-boundary temperature (Sect. 2.8, Eq. 18)
 * ``run_loop``            -- the iteration cycle of Sect. 2.8 (resumable from T_R, W)
 
-Parity unpinned: the Philox stream is pinned only statistically (its published
-known-answer vectors are not available here); every other function has pins in
-``tests/test_oracle_*.py``.
+Every function has pins in ``tests/test_oracle_*.py`` (Philox4x32-10 against
+its published known-answer values, ``tests/golden/philox4x32_10_kat.txt``).
 """
 from __future__ import annotations
 

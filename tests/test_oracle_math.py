@@ -1,12 +1,15 @@
 """Pins of the oracle's elementary functions and of its random-draw stream.
 
 ln / exp are pinned against numpy's libm (an independent implementation):
-the oracle's own series must stay within 2 ulp.  The Philox4x32-10 stream
-(Salmon et al. 2011) is pinned statistically -- its published known-answer
-vectors are not available here, so bit-exact conformance to the published
-generator is unpinned (the CUDA side implements the same definition
-independently and parity tests compare the two streams).
+the oracle's own series must stay within 2 ulp.  The Philox4x32-10 block
+function (Salmon et al. 2011) is pinned bit for bit to its published
+known-answer values (tests/golden/philox4x32_10_kat.txt), and the draw
+stream built on it statistically (uniformity, independence, avalanche); the
+CUDA side implements the same definition independently and the parity tests
+compare the two streams.
 """
+import os
+
 import numpy as np
 import pytest
 from scipy import stats
@@ -82,3 +85,16 @@ def test_philox_avalanche_and_key_dependence():
         assert not np.array_equal(oracle.philox(ctr, k2), o)
     m = np.mean(flips)
     assert 60 < m < 68, m  # half of 128 output bits on average
+
+
+def test_philox_known_answers():
+    """The published known-answer values of Philox4x32-10 (tests/golden/
+    philox4x32_10_kat.txt): the oracle's generator is the published one, word
+    for word, so every draw of both sides is pinned."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(x, 16) for x in r]
+        out = oracle.philox(w[0:4], w[4:6])
+        assert [int(v) for v in out] == w[6:10], r
