@@ -228,6 +228,17 @@ mc_status mc_run_iteration(mc_model *m, uint64_t seed, uint32_t iteration, uint6
 mc_status mc_run_iteration_range(mc_model *m, uint64_t seed, uint32_t iteration, uint64_t first_packet,
                                  uint64_t n_packets, uint64_t n_total, double t_inner);
 
+/* Ask this model's transport launches to stop (stop = 1) or withdraw the
+ * request (stop = 0).  A single-model launch that is running, or starts,
+ * while the request stands stops at its next look at it (each warp looks
+ * every 256 loop iterations: microseconds to a millisecond), leaving
+ * unfinished packets, and the run's reads return MC_ERR_TIMEOUT with a
+ * message naming the cancel.  The request stands until withdrawn.  The call
+ * writes one word of pinned host memory and may come from any host thread
+ * while the launch runs.  Batched launches do not look at it.
+ *  Errors: MC_ERR_INVALID_ARG (m NULL, stop not 0 or 1). */
+mc_status mc_cancel(mc_model *m, int32_t stop);
+
 /* Update T_R and W from the last run's estimators (Eqs. 15-16) on the device;
  * shells with no path length keep their values.  The next run recomputes the
  * Sobolev depths when they are not given.  Copies the new values to t_rad_out

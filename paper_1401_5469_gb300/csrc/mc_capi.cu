@@ -75,6 +75,11 @@ void free_all(mc_model *m) {
   m->allocations.clear();
 }
 
+// Why a transport launch stopped early (the kernel's flag word).
+const char *stop_message(unsigned long long flag) {
+  return flag == 2ull ? "transport launch stopped by mc_cancel" : "transport kernel stopped at its deadline";
+}
+
 mc_status recompute_tau(mc_model *m) {
   PlasmaParams pp{};
   pp.S = static_cast<int32_t>(m->S);
@@ -341,6 +346,7 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
     cudaStreamSynchronize(m->stream);
     free_all(m);
     cudaStreamSynchronize(m->stream);
+    if (m->cancel_host) cudaFreeHost(m->cancel_host);
     for (int i = 0; i < kNEv; ++i) cudaEventDestroy(m->ev[i]);
     if (m->own_stream) cudaStreamDestroy(m->stream);
     delete m;
@@ -373,6 +379,16 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
            alloc_n(m, &m->row_info, L);
   }
   if (ok) ok = alloc_n(m, &m->n_e, S);
+  if (ok) {  // the stop request: one pinned host word the kernels can read
+    void *h = nullptr, *d = nullptr;
+    ok = cudaHostAlloc(&h, sizeof(uint32_t), cudaHostAllocMapped) == cudaSuccess;
+    if (ok) {
+      m->cancel_host = static_cast<uint32_t *>(h);
+      *static_cast<volatile uint32_t *>(m->cancel_host) = 0u;
+      ok = cudaHostGetDevicePointer(&d, h, 0) == cudaSuccess;
+      m->cancel_dev = static_cast<const uint32_t *>(d);
+    }
+  }
   if (ok && ion_mode != MC_ION_FIXED) {
     const size_t E = atomic->n_elements, J = atomic->n_stages;
     m->ion_mode = ion_mode;
@@ -712,6 +728,7 @@ void model_fill_transport(const mc_model *m, TransportParams &p, uint64_t seed, 
   p.max_segments = m->run.max_segments;
   p.rec_status = m->rec_status; p.rec_nu = m->rec_nu; p.rec_e = m->rec_e; p.rec_cnt = m->rec_cnt;
   p.timeout_ns = m->run.timeout_ns;
+  p.cancel = m->cancel_dev;
   p.shell32 = m->shell32;
   p.est_fix = m->est_fix;
   p.inv_nu_ref = 1.0 / p.nu_scale;
@@ -780,7 +797,7 @@ mc_status mc_read_estimators(mc_model *m, double *j_est, double *nu_bar, double 
   if (norm) std::memcpy(norm, m->host_norm.data(), m->S * sizeof(double));
   unsigned long long flag = 0;
   cudaMemcpy(&flag, m->counters + kNStats + 1, sizeof(flag), cudaMemcpyDeviceToHost);
-  if (flag) return fail(m, MC_ERR_TIMEOUT, "transport kernel stopped at its deadline");
+  if (flag) return fail(m, MC_ERR_TIMEOUT, stop_message(flag));
   return MC_OK;
 }
 
@@ -807,7 +824,7 @@ mc_status mc_read_spectrum(mc_model *m, double *spectrum, mc_packet_stats *stats
     stats->e_scatters = c[kStEScatters];
     stats->shell_crossings = c[kStShellCrossings];
   }
-  if (c[kNStats + 1]) return fail(m, MC_ERR_TIMEOUT, "transport kernel stopped at its deadline");
+  if (c[kNStats + 1]) return fail(m, MC_ERR_TIMEOUT, stop_message(c[kNStats + 1]));
   return c[kStCapped] ? MC_WARN_CAPPED : MC_OK;
 }
 
@@ -971,9 +988,16 @@ void mc_model_destroy(mc_model *m) {
   cudaStreamSynchronize(m->stream);
   free_all(m);
   cudaStreamSynchronize(m->stream);
+  if (m->cancel_host) cudaFreeHost(m->cancel_host);
   for (int i = 0; i < kNEv; ++i) cudaEventDestroy(m->ev[i]);
   if (m->own_stream) cudaStreamDestroy(m->stream);
   delete m;
+}
+
+mc_status mc_cancel(mc_model *m, int32_t stop) {
+  if (!m || (stop != 0 && stop != 1)) return MC_ERR_INVALID_ARG;
+  *static_cast<volatile uint32_t *>(m->cancel_host) = static_cast<uint32_t>(stop);
+  return MC_OK;
 }
 
 }  // extern "C"

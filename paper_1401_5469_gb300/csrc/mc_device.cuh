@@ -85,6 +85,14 @@ __device__ __forceinline__ bool strictly_negative(double v) {
   return b < 0 && b != kRawBelowZero;
 }
 
+// A 32-bit word the host may write while the kernel runs (pinned, mapped
+// host memory): system-scope load, so the host's store becomes visible.
+__device__ __forceinline__ uint32_t load_sys_u32(const uint32_t *a) {
+  uint32_t v;
+  asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

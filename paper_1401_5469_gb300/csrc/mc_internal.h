@@ -100,6 +100,7 @@ struct TransportParams {
   const unsigned long long *batch_prefix;  // [n_models + 1] packet offsets of the models
   int32_t n_models;
   unsigned long long timeout_ns;     // 0 = none
+  const uint32_t *cancel;            // mapped host word: nonzero stops the launch (or nullptr)
   unsigned long long *flags;         // [0] deadline hit, [1] work queue empty (ns),
                                      // [2] last warp done (ns), [3] first warp start (ns)
   // virtual packets (Sect. 2.9; binary64 kernel)

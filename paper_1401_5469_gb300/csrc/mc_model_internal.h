@@ -54,6 +54,8 @@ struct mc_model {
   int32_t *ion_of = nullptr;
   double *chi_erg = nullptr, *zeta = nullptr, *n_element = nullptr, *ion_phi = nullptr;
   double *n_e = nullptr;  // [S] electron densities the Thomson opacity is built from
+  uint32_t *cancel_host = nullptr;  // pinned, mapped: the stop request (mc_cancel)
+  const uint32_t *cancel_dev = nullptr;
   double *norm = nullptr;
   double *j_est = nullptr, *nu_bar = nullptr, *j_blue = nullptr, *spectrum = nullptr;
   double *spectrum_v = nullptr;  // [bins + 2] virtual-packet spectrum (allocated on first use)

@@ -292,6 +292,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lanemask_lt = (1u << lane) - 1u;
   const unsigned long long t_start = global_ns();
+  uint32_t polls = 0u;  // loop iterations between looks at the host's stop request
   if (lane == 0u) atomicCAS(p.flags + 3, 0ull, t_start);
 
   Packet pk;
@@ -342,6 +343,15 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       late = __shfl_sync(0xffffffffu, late, 0);
       if (late) {
         if (lane == 0u) atomicExch(p.flags, 1ull);
+        break;
+      }
+    }
+    if (p.cancel && (++polls & 255u) == 0u) {  // the host's stop request (mc_cancel)
+      uint32_t stop = 0u;
+      if (lane == 0u) stop = load_sys_u32(p.cancel);
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      if (stop) {
+        if (lane == 0u) atomicExch(p.flags, 2ull);
         break;
       }
     }

@@ -39,7 +39,7 @@ COUNTER_NAMES = ("segments", "line_checks", "resonances", "line_interactions", "
 EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_run_iteration_range",
             "mc_update_radiation_field",
             "mc_read_estimators", "mc_read_spectrum", "mc_read_packets", "mc_read_plasma",
-            "mc_read_ionization",
+            "mc_read_ionization", "mc_cancel",
             "mc_read_timing", "mc_read_transport_phases", "mc_launch_count", "mc_synchronize", "mc_model_destroy",
             "mc_status_string", "mc_last_error_message", "mc_transport_noalloc",
             "mc_batch_create", "mc_batch_run_iteration", "mc_batch_synchronize",
@@ -175,6 +175,8 @@ def load(build_if_missing: bool = True):
     L.mc_read_plasma.argtypes = [vp, vp, vp, vp]
     L.mc_read_ionization.restype = i32
     L.mc_read_ionization.argtypes = [vp, vp, vp]
+    L.mc_cancel.restype = i32
+    L.mc_cancel.argtypes = [vp, i32]
     L.mc_read_timing.restype = i32
     L.mc_read_timing.argtypes = [vp, vp]
     L.mc_read_transport_phases.restype = i32
@@ -547,6 +549,10 @@ class Model:
         tau = np.zeros((self.S, self.L))
         mc_read_plasma(self.h, t, w, tau)
         return t, w, tau
+
+    def cancel(self, stop: bool = True):
+        """mc_cancel: ask running and later launches to stop (or withdraw)."""
+        return _check(load().mc_cancel(self.h, int(bool(stop))), self.h)
 
     def ionization(self):
         """mc_read_ionization: electron densities [S] and ion densities [S, I]

@@ -91,6 +91,7 @@ def test_batch_calls_reject_null_arguments():
     assert L.mc_batch_autotune(None, None, None, None, None, None, None, None) == mc.MC_ERR_INVALID_ARG
     assert L.mc_batch_run_iteration(None, None, None, None, None, 1) == mc.MC_ERR_INVALID_ARG
     assert L.mc_batch_capture_graph(None, 1) == mc.MC_ERR_INVALID_ARG
+    assert L.mc_cancel(None, 1) == mc.MC_ERR_INVALID_ARG
     h = C.c_void_p()
     assert L.mc_batch_create(None, 0, C.byref(h)) == mc.MC_ERR_INVALID_ARG
     assert not h.value

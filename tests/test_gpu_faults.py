@@ -4,9 +4,13 @@
   returns MC_ERR_OOM with a message, and every block it had obtained is
   handed back through the allocator's free;
 * after a successful create, run and destroy, the allocator holds nothing;
+* mc_cancel stops a running launch within milliseconds (its reads report
+  MC_ERR_TIMEOUT naming the cancel), stops a launch started while the request
+  stands, and once withdrawn the model runs normally again;
 * the transport deadline: covered by tests/test_gpu_parity.py.
 """
 import ctypes as C
+import time
 
 import numpy as np
 import pytest
@@ -102,3 +106,36 @@ def test_run_and_destroy_release_everything(env):
     L.mc_model_destroy(h)
     torch.cuda.synchronize()
     assert al.calls > 10 and not al.live
+
+
+def test_cancel_stops_running_and_later_launches(env):
+    torch, mc = env
+    spec = synth.downbranch_model(n_lines=100_000, n_packets=300_000)
+    n = spec.n_packets
+    m = mc.Model(spec)
+    m.set_plasma()
+    m.run_iteration(1, 0, n, spec.t_inner)
+    m.synchronize()
+    t0 = time.perf_counter()
+    m.run_iteration(1, 1, n, spec.t_inner)
+    m.synchronize()
+    full = time.perf_counter() - t0
+    m.run_iteration(1, 2, n, spec.t_inner)  # asynchronous
+    time.sleep(0.2 * full)
+    t0 = time.perf_counter()
+    m.cancel()
+    with pytest.raises(mc.MCError) as ei:
+        m.estimators()
+    stopped = time.perf_counter() - t0
+    assert ei.value.code == mc.MC_ERR_TIMEOUT and "mc_cancel" in str(ei.value)
+    assert stopped < 0.5 * full, (stopped, full)
+    m.run_iteration(1, 3, n, spec.t_inner)  # starts while the request stands
+    with pytest.raises(mc.MCError) as ei:
+        m.spectrum()
+    assert ei.value.code == mc.MC_ERR_TIMEOUT
+    m.cancel(False)
+    m.run_iteration(1, 4, 2000, spec.t_inner)
+    m.estimators()
+    _, stats, rc = m.spectrum()
+    assert stats["escaped"] + stats["reabsorbed"] == 2000
+    m.close()
