@@ -66,10 +66,10 @@ L2_BYTES = 129 * 2**20
 # kernel built from these sources only: with any other source hash the
 # bench reports traffic as null.
 TRAFFIC_CAPTURE = {
-    "dram_bytes_per_launch": 619.47e6 + 111.29e6,
+    "dram_bytes_per_launch": 625.95e6 + 112.66e6,
     "sources": ("paper_1401_5469_gb300/csrc/mc_transport.cu", "paper_1401_5469_gb300/csrc/mc_device.cuh",
                 "paper_1401_5469_gb300/csrc/mc_internal.h"),
-    "sha256": "c1fd170e893a6786299c0a3e6c53eea352f6a1baa5495bad19cdfc4d8e268c6b",
+    "sha256": "084d987e58e2d50c1bdca8291767a83ddbed811c6efbd79c541c3b08ff2f4445",
 }
 
 
@@ -78,7 +78,7 @@ TRAFFIC_CAPTURE = {
 # counters on the 1e5-packet case of this model (profiles/
 # transport_fp64_downbranch_1e5_fp64_ops.md); null for other sources.
 FP64_OPS_CAPTURE = {
-    "lane_ops_per_segment": 76.64,
+    "lane_ops_per_segment": 76.71,
     "sources": TRAFFIC_CAPTURE["sources"],
     "sha256": TRAFFIC_CAPTURE["sha256"],
 }
