@@ -7,11 +7,14 @@
 // to the injection energy) and the frame factors are binary32.  Binary64 is
 // kept where the method needs it: the lab and comoving frequencies, the
 // Sobolev-resonance comparison against the frequency-sorted line list
-// (integer keys of binary64 values), the frequency thresholds that the optical
-// depth is accumulated into, and the estimator sums.  The lab frequency after
-// a re-emission is nu_c / D to binary64 accuracy (Newton step on the binary32
-// reciprocal), so the comoving frequency at the emission point is the emitting
-// line's frequency.
+// (integer keys of binary64 values) and the frequency thresholds that the
+// optical depth is accumulated into.  J, nu_bar and J_blue are summed exactly
+// as 64-bit fixed point from binary32 contributions (order-independent).  The
+// lab frequency after a re-emission is nu_c / D to binary64 accuracy (Newton
+// step on the binary32 reciprocal), so the comoving frequency at the emission
+// point is the emitting line's frequency.  Conversions between the two
+// formats are done on the bit patterns with integer operations (on this GPU a
+// conversion instruction takes the binary64 pipe).
 //
 // Batched launch.  Packets of all models are claimed from one queue (models
 // laid out by a prefix sum of their packet counts, largest first so that the
