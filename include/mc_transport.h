@@ -157,7 +157,7 @@ typedef struct {
 
 /* Run options. */
 typedef struct {
-    int32_t line_mode;          /* MC_LINE_* (MC_LINE_MACROATOM: binary64 only) */
+    int32_t line_mode;          /* MC_LINE_* */
     int32_t precision;          /* MC_PRECISION_* */
     int32_t j_blue;             /* 1: accumulate J_blue estimators (Eq. 17) */
     int32_t record_packets;     /* 1: keep per-packet fates for mc_read_packets */

@@ -188,11 +188,9 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
   if (run->line_mode != MC_LINE_SCATTER && run->line_mode != MC_LINE_DOWNBRANCH &&
       run->line_mode != MC_LINE_MACROATOM)
     return fail(nullptr, MC_ERR_INVALID_ARG, "unknown line_mode");
-  if (run->line_mode == MC_LINE_MACROATOM && run->precision != MC_PRECISION_FP64)
-    return fail(nullptr, MC_ERR_UNSUPPORTED, "macro-atom mode runs in the binary64 kernel");
   if (run->precision != MC_PRECISION_FP64 && run->precision != MC_PRECISION_MIXED)
     return fail(nullptr, MC_ERR_INVALID_ARG, "unknown precision");
-  if (run->precision == MC_PRECISION_MIXED && run->line_mode == MC_LINE_DOWNBRANCH &&
+  if (run->precision == MC_PRECISION_MIXED && run->line_mode != MC_LINE_SCATTER &&
       !(atomic && atomic->dbr_offset))
     return fail(nullptr, MC_ERR_INVALID_ARG, "mixed-precision downbranch needs the branching table");
   if (run->spec_bins == 0 || !(run->spec_nu_hi > run->spec_nu_lo) || !(run->spec_nu_lo >= 0.0))

@@ -50,6 +50,9 @@ struct MCtx {
   const double *nu;
   const float *tau32;
   const unsigned long long *row_info;
+  const int32_t *line_row;           // macro atom: upper level of each line
+  const MaRow *ma_row;               // macro atom: level table
+  const MaJump *ma_jump;             // macro atom: jump entries
   const DbrRec *bucket, *rec;
   double *j_blue, *j_est, *nu_bar, *spectrum;
   unsigned long long *stats;
@@ -77,6 +80,9 @@ __device__ __forceinline__ void load_ctx(MCtx &c, const TransportParams &q, cons
   c.nu = q.nu;
   c.tau32 = q.tau32;
   c.row_info = q.row_info;
+  c.line_row = q.line_row;
+  c.ma_row = q.ma_row;
+  c.ma_jump = q.ma_jump;
   c.bucket = q.dbr_bucket;
   c.rec = q.dbr_rec;
   c.j_blue = q.j_blue;
@@ -172,6 +178,31 @@ __device__ __forceinline__ void pick_m(const MCtx &c, unsigned long long rinfo, 
 }
 
 __device__ __forceinline__ float max0f(float v) { return v > 0.0f ? v : 0.0f; }
+
+// Macro atom (Sect. 2.5): the binary64 kernel's walk (integer thresholds, the
+// same draws in the same order) on a lane's model context; returns the
+// branching-row info of the level the atom deactivates from.
+__device__ __forceinline__ unsigned long long macroatom_walk_m(const MCtx &c, int32_t row, DrawStream &ds) {
+  for (uint32_t n = 0; n < kMaMaxJumps; ++n) {
+    const MaRow *mr = c.ma_row + row;
+    const unsigned long long thr = __ldg(&mr->jump_thr);
+    const uint2 jb = __ldg(reinterpret_cast<const uint2 *>(&mr->jump_begin));  // begin, length
+    const unsigned long long za = ds.next_u53();
+    if (!(za < thr)) {
+      const uint2 db = __ldg(reinterpret_cast<const uint2 *>(&mr->dbr_begin));
+      return static_cast<unsigned long long>(db.x) | (static_cast<unsigned long long>(db.y) << 32);
+    }
+    const unsigned long long zb = ds.next_u53();
+    const MaJump *jp = c.ma_jump + jb.x;
+    int32_t next = __ldg(&jp[jb.y - 1].target);
+    for (uint32_t k = 0; k < jb.y; ++k) {
+      if (zb < __ldg(&jp[k].thr)) { next = __ldg(&jp[k].target); break; }
+    }
+    row = next;
+  }
+  const uint2 db = __ldg(reinterpret_cast<const uint2 *>(&c.ma_row[row].dbr_begin));
+  return static_cast<unsigned long long>(db.x) | (static_cast<unsigned long long>(db.y) << 32);
+}
 
 // x mu at the shell exit, +sqrt(x_out^2 - q) or -sqrt(x_in^2 - q).
 __device__ __forceinline__ float shell_exit_f(float q, bool inner, float xi2, float xo2) {
@@ -485,9 +516,12 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
         float inv_nu_c;
         if (kind == kLineEvent) {
           pk.cnt[3] += 1u;
-          if (MODE == 1) {
+          if (MODE >= 1) {
+            // MODE 2: macro atom, internal jumps before the emission pick
+            const unsigned long long rinfo_em =
+                MODE == 2 ? macroatom_walk_m(c, __ldg(c.line_row + j), ds) : rinfo_hit;
             int32_t emit;
-            pick_m(c, rinfo_hit, ds.next_u53(), nu_c, inv_nu_c, emit);
+            pick_m(c, rinfo_em, ds.next_u53(), nu_c, inv_nu_c, emit);
             pk.next_line = emit + 1;
           } else {
             nu_c = nu_hit;
@@ -568,6 +602,10 @@ const void *select_m(int line_mode, bool jb, bool rec) {
   if (line_mode == 0) {
     if (jb) return rec ? kptr<0, true, true, MINB>() : kptr<0, true, false, MINB>();
     return rec ? kptr<0, false, true, MINB>() : kptr<0, false, false, MINB>();
+  }
+  if (line_mode == 2) {
+    if (jb) return rec ? kptr<2, true, true, MINB>() : kptr<2, true, false, MINB>();
+    return rec ? kptr<2, false, true, MINB>() : kptr<2, false, false, MINB>();
   }
   if (jb) return rec ? kptr<1, true, true, MINB>() : kptr<1, true, false, MINB>();
   return rec ? kptr<1, false, true, MINB>() : kptr<1, false, false, MINB>();
