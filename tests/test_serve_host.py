@@ -1,0 +1,146 @@
+"""Host logic of the continuous-batching service, on the CPU.
+
+The GPU models and batches are replaced by stand-ins that record what the
+service asks of them, so admission and retirement can be checked without a
+device: requests are admitted first come, first served while the HBM budget
+and the per-tick packet budget allow (the head of the queue is never skipped
+for a smaller request behind it); a request larger than the whole budget is
+still admitted when nothing else is resident; each tick advances every
+resident model by exactly one iteration, with its own seed and iteration
+index; a model leaves after its last iteration, its footprint is released
+and the batch is rebuilt for the models that remain.
+"""
+import numpy as np
+import pytest
+
+from paper_1401_5469_gb300 import serve, synth
+
+
+class _FakeModel:
+    live = 0
+
+    def __init__(self, spec, precision=None, j_blue=None, stream=None):
+        self.spec, self.S, self.closed = spec, spec.n_shells, False
+        self.iterations = []
+        _FakeModel.live += 1
+
+    def set_plasma(self, *a, **k):
+        pass
+
+    def estimators(self, j_blue=False):
+        return np.zeros(self.S), np.zeros(self.S), None, np.ones(self.S)
+
+    def spectrum(self):
+        return np.zeros(self.spec.spec_bins + 2), {}, 0
+
+    def close(self):
+        assert not self.closed
+        self.closed = True
+        _FakeModel.live -= 1
+
+
+class _FakeBatch:
+    created = []
+
+    def __init__(self, models):
+        self.models, self.closed = list(models), False
+        _FakeBatch.created.append(self)
+
+    def run_iteration(self, seeds, iterations, n_packets, t_inner, update=True):
+        assert not self.closed and update
+        for m, s, it, n in zip(self.models, seeds, iterations, n_packets):
+            assert not m.closed and n == m.spec.n_packets
+            m.iterations.append((s, it))
+
+    def synchronize(self):
+        pass
+
+    def transport_ms(self):
+        return 1.0
+
+    def close(self):
+        self.closed = True
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    _FakeModel.live = 0
+    _FakeBatch.created = []
+    monkeypatch.setattr(serve.mc, "Model", _FakeModel)
+    monkeypatch.setattr(serve.mc, "Batch", _FakeBatch)
+    monkeypatch.setattr(serve, "_radiation_field", lambda m: (np.zeros(m.S), np.zeros(m.S)))
+    return serve
+
+
+def _spec(n_lines, n_packets):
+    return synth.scatter_model(n_lines=n_lines, n_shells=4, n_packets=n_packets)
+
+
+def test_fifo_admission_under_the_hbm_budget(fake):
+    small, big = _spec(200, 100), _spec(4000, 100)
+    fs = serve.model_footprint_bytes(small, True)
+    fb = serve.model_footprint_bytes(big, True)
+    srv = serve.Server(hbm_budget_bytes=fb + fs, j_blue=True)
+    reqs = [serve.Request(rid=0, spec=big, n_iterations=2, seed=1),
+            serve.Request(rid=1, spec=big, n_iterations=1, seed=2),   # does not fit beside rid 0
+            serve.Request(rid=2, spec=small, n_iterations=1, seed=3)]  # would fit, must wait its turn
+    for r in reqs:
+        srv.submit(r)
+    assert srv.step(0.0) == 1 and list(srv.active) == [0]
+    assert srv.used == fb and srv.used <= srv.budget
+    assert srv.step(1.0) == 1            # rid 0 ends; rids 1, 2 still queued (FIFO head blocked)
+    assert [r.rid for r in srv.done] == [0] and srv.used == 0
+    assert srv.step(2.0) == 2            # both fit now: fb + fs <= budget
+    assert sorted(r.rid for r in srv.done) == [0, 1, 2] and not srv.active and srv.used == 0
+    assert _FakeModel.live == 0
+
+
+def test_each_tick_advances_every_model_once_with_its_own_draws(fake):
+    specs = [_spec(300, 50 + k) for k in range(3)]
+    srv = serve.Server(hbm_budget_bytes=1e12)
+    reqs = [serve.Request(rid=k, spec=s, n_iterations=k + 1, seed=100 + k) for k, s in enumerate(specs)]
+    for r in reqs:
+        srv.submit(r)
+    models = {}
+    while srv.queue or srv.active:
+        srv.step(float(srv.ticks))
+        for rid, (req, m, _) in srv.active.items():
+            models[rid] = m
+    # every model ran iterations 0 .. n-1 with its own seed, one per tick
+    assert srv.ticks == 3
+    for k, r in enumerate(reqs):
+        assert r.done_iterations == r.n_iterations and r.finished is not None
+    assert _FakeModel.live == 0
+    # the batch was rebuilt whenever the resident set changed, and closed
+    assert len(_FakeBatch.created) == 3 and all(b.closed for b in _FakeBatch.created)
+    seen = {}
+    for b in _FakeBatch.created:
+        for m in b.models:
+            seen.setdefault(id(m), m)
+    runs = sorted((m.spec.n_packets, m.iterations) for m in seen.values())
+    assert runs == [(50, [(100, 0)]), (51, [(101, 0), (101, 1)]), (52, [(102, 0), (102, 1), (102, 2)])]
+
+
+def test_tick_packet_budget_and_oversized_request(fake):
+    a, b = _spec(200, 600), _spec(200, 600)
+    huge = _spec(8000, 10)
+    srv = serve.Server(hbm_budget_bytes=serve.model_footprint_bytes(a, True) * 3, max_tick_packets=1000)
+    for k, s in enumerate((a, b)):
+        srv.submit(serve.Request(rid=k, spec=s, n_iterations=1, seed=k))
+    srv.step(0.0)
+    # the second request would push the tick past 1000 packets: it waits
+    assert [r.rid for r in srv.done] == [0] and list(srv.queue)[0].rid == 1
+    srv.step(1.0)
+    assert [r.rid for r in srv.done] == [0, 1]
+    # a request larger than the whole budget runs alone rather than never
+    assert serve.model_footprint_bytes(huge, True) > srv.budget
+    srv.submit(serve.Request(rid=9, spec=huge, n_iterations=1, seed=9))
+    assert srv.step(2.0) == 1 and srv.done[-1].rid == 9
+    srv.close()
+    assert _FakeModel.live == 0
+
+
+def test_percentiles():
+    p = serve.percentiles([1.0, 2.0, 3.0, 4.0, None])
+    assert p["p50"] == pytest.approx(2.5) and p["p99"] == pytest.approx(3.97)
+    assert serve.percentiles([None])["p50"] is None
