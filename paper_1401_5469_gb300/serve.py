@@ -48,6 +48,11 @@ def model_footprint_bytes(spec, j_blue: Optional[bool] = None,
     b += nnz * (4 + 4 + 8 + 32 + 32)   # branching table + guide records
     if spec.n_ions:
         b += spec.n_ions * spec.n_levels * (8 + 8 + 1) + S * spec.n_ions * (8 + 8 * spec.n_levels)
+    if getattr(spec, "ma_jump_p", None) is not None:  # macro-atom level and jump tables
+        b += spec.n_ions * spec.n_levels * 24 + int(np.asarray(spec.ma_jump_target).size) * 16
+    if getattr(spec, "ionization_mode", 0):  # ionization tables and scratch
+        E, J = int(spec.n_elements), int(spec.n_stages)
+        b += 4 * E * J + 16 * E * (J - 1) + 8 * S * E + 8 * S * E * (J - 1)
     b += 8 * (spec.spec_bins + 2) + 64 * S + 16 * 1024
     return int(b)
 

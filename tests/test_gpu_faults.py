@@ -4,6 +4,8 @@
   returns MC_ERR_OOM with a message, and every block it had obtained is
   handed back through the allocator's free;
 * after a successful create, run and destroy, the allocator holds nothing;
+* the serving loop's footprint estimate (its HBM admission budget) covers
+  every byte a model obtains, and is not more than 25% above it;
 * mc_cancel stops a running launch within milliseconds (its reads report
   MC_ERR_TIMEOUT naming the cancel), stops a launch started while the request
   stands, and once withdrawn the model runs normally again;
@@ -57,6 +59,8 @@ class _Allocator:
             t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device="cuda")
             self.live[t.data_ptr()] = t
             return t.data_ptr()
+
+        self.bytes = lambda: sum(t.numel() for t in self.live.values())
 
         def free(ptr, ctx):
             self.live.pop(ptr)
@@ -139,3 +143,28 @@ def test_cancel_stops_running_and_later_launches(env):
     _, stats, rc = m.spectrum()
     assert stats["escaped"] + stats["reabsorbed"] == 2000
     m.close()
+
+
+@pytest.mark.parametrize("precision,j_blue,kind", [(1, True, "downbranch"), (1, False, "downbranch"),
+                                                   (0, True, "downbranch"), (1, True, "macroatom")])
+def test_footprint_estimate_covers_the_allocations(env, precision, j_blue, kind):
+    torch, mc = env
+    from paper_1401_5469_gb300 import serve
+    make = synth.downbranch_model if kind == "downbranch" else synth.macroatom_model
+    spec = make(n_lines=30000, n_shells=15, n_packets=5000, j_blue=j_blue)
+    keep = []
+    g, l, a, r = _descs(mc, spec, keep)
+    r.precision, r.j_blue, r.record_packets = precision, int(j_blue), 0
+    L = mc.load()
+    al = _Allocator(torch, mc)
+    h = C.c_void_p()
+    assert L.mc_model_create(C.byref(g), C.byref(l), C.byref(a), C.byref(r), C.byref(al.c), None,
+                             C.byref(h)) == 0
+    assert L.mc_set_plasma(h, None, None, None) == 0
+    assert L.mc_run_iteration(h, 5, 0, spec.n_packets, spec.t_inner) == 0
+    assert L.mc_synchronize(h) == 0
+    used = al.bytes()
+    est = serve.model_footprint_bytes(spec, j_blue, precision)
+    L.mc_model_destroy(h)
+    torch.cuda.synchronize()
+    assert used <= est <= 1.25 * used, (used, est)
