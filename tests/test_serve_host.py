@@ -144,3 +144,35 @@ def test_percentiles():
     p = serve.percentiles([1.0, 2.0, 3.0, 4.0, None])
     assert p["p50"] == pytest.approx(2.5) and p["p99"] == pytest.approx(3.97)
     assert serve.percentiles([None])["p50"] is None
+
+
+def test_iterate_applies_luminosity_matching_every_third_iteration(monkeypatch):
+    """mc.Model.iterate's host logic with the device calls stubbed: T_inner
+    changes only after iterations 3, 6, ... by (L_req / L_emitted)^(1/4)
+    (mc_t_inner_update from the C library, no GPU needed), each iteration
+    runs with the T_inner then current, and the radiation field is updated
+    after every iteration."""
+    import oracle
+    from paper_1401_5469_gb300 import mc
+    calls = []
+    monkeypatch.setattr(mc, "mc_update_radiation_field", lambda h, t, w: calls.append("update"))
+
+    class _M(mc.Model):
+        def __init__(self):
+            self.h = None
+            self.lum = iter([2.0, 3.0, 5.0, 7.0, 11.0, 13.0, 17.0])
+
+        def run_iteration(self, seed, iteration, n_packets, t_inner):
+            calls.append(("run", iteration, t_inner))
+
+        def emitted_luminosity(self):
+            return next(self.lum)
+
+    m = _M()
+    used, t_next = m.iterate(7, 7, 100, 1.0e4, l_requested=4.0)
+    t3 = oracle.t_inner_update(1.0e4, 4.0, 2.0)      # after iteration 2: L_emitted of that iteration
+    t6 = oracle.t_inner_update(t3, 4.0, 3.0)         # after iteration 5
+    assert used == [1.0e4] * 3 + [t3] * 3 + [t6]
+    assert t_next == t6
+    assert calls.count("update") == 7
+    assert [c[1] for c in calls if c != "update"] == list(range(7))
