@@ -8,7 +8,8 @@ resident models together, one iteration each per tick.  Requests that arrive
 while others are on the GPU are admitted first come, first served at the next
 tick while the HBM budget (and the optional per-tick packet budget) allows, so
 their iterations overlap on the device with the models already running; a
-model leaves as soon as its last iteration is done.
+model leaves as soon as its last iteration is done, or when its request is
+withdrawn between ticks (its memory and packet budget are released).
 
 In mixed precision a tick is one batched transport launch for all resident
 models (a captured CUDA graph).  In binary64 a tick launches every resident
@@ -74,6 +75,7 @@ class Request:
     spectrum: Optional[np.ndarray] = None
     keep_history: bool = False
     history: List = dataclasses.field(default_factory=list)
+    aborted: bool = False
 
     @property
     def latency(self) -> Optional[float]:
@@ -105,6 +107,7 @@ class Server:
         self.batch: Optional[mc.Batch] = None
         self.batch_ids: List[int] = []
         self.done: List[Request] = []
+        self.aborted: List[Request] = []
         self.ticks = 0
         self.tick_ms: List[float] = []
         self.transport_ms: List[float] = []
@@ -130,6 +133,30 @@ class Server:
             self.active[req.rid] = (req, m, need)
             self.used += need
             self.tick_packets += req.spec.n_packets
+
+    def withdraw(self, rid: int) -> bool:
+        """Abort request rid between ticks: drop it from the queue, or release
+        its resident model (footprint and packet budget freed; the batch is
+        rebuilt at the next tick).  Returns whether the request was found."""
+        for r in self.queue:
+            if r.rid == rid:
+                self.queue.remove(r)
+                r.aborted = True
+                self.aborted.append(r)
+                return True
+        if rid not in self.active:
+            return False
+        if self.batch is not None:
+            self.batch.close()  # the batch goes before its models
+            self.batch = None
+            self.batch_ids = []
+        req, m, need = self.active.pop(rid)
+        m.close()
+        self.used -= need
+        self.tick_packets -= req.spec.n_packets
+        req.aborted = True
+        self.aborted.append(req)
+        return True
 
     def _retire(self, rid: int, now: float):
         req, m, need = self.active.pop(rid)

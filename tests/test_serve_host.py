@@ -176,3 +176,23 @@ def test_iterate_applies_luminosity_matching_every_third_iteration(monkeypatch):
     assert t_next == t6
     assert calls.count("update") == 7
     assert [c[1] for c in calls if c != "update"] == list(range(7))
+
+
+def test_withdrawn_requests_release_their_resources(fake):
+    specs = [_spec(300, 100 + k) for k in range(4)]
+    srv = serve.Server(hbm_budget_bytes=2.5 * serve.model_footprint_bytes(specs[0], True))
+    for k, s in enumerate(specs):
+        srv.submit(serve.Request(rid=k, spec=s, n_iterations=3, seed=k))
+    srv.step(0.0)
+    assert sorted(srv.active) == [0, 1] and [r.rid for r in srv.queue] == [2, 3]
+    used_before = srv.used
+    assert srv.withdraw(1)                 # resident: model released, budget freed
+    assert srv.withdraw(3)                 # queued: simply dropped
+    assert not srv.withdraw(42)
+    assert srv.used < used_before and 1 not in srv.active
+    assert [r.rid for r in srv.aborted] == [1, 3] and all(r.aborted for r in srv.aborted)
+    while srv.queue or srv.active:
+        srv.step(float(srv.ticks))
+    assert sorted(r.rid for r in srv.done) == [0, 2]
+    assert all(r.done_iterations == 3 for r in srv.done)
+    assert srv.used == 0 and srv.tick_packets == 0 and _FakeModel.live == 0
