@@ -86,6 +86,12 @@ MUTANTS = [
     ("macro-atom jump target off by one", "if (zb < m->ma_jump_cdf[k]) { next = m->ma_jump_target[k]; break; }",
      "if (zb < m->ma_jump_cdf[k]) { next = m->ma_jump_target[k > b ? k - 1 : k]; break; }", 1,
      "tests/test_oracle_macroatom.py::test_walks_match_the_absorbing_markov_chain"),
+    ("T_inner update with a square root instead of a fourth root",
+     "return t_inner * sqrt(sqrt(l_requested / l_emitted));", "return t_inner * sqrt(l_requested / l_emitted);", 1,
+     "tests/test_oracle_luminosity.py::test_one_update_reaches_the_requested_luminosity_in_free_streaming"),
+    ("Eq. 18 with r instead of r^2", "double x = l_outer / ((((4.0 * PI_D) * r_inner) * r_inner) * SIGMA_SB);",
+     "double x = l_outer / (((4.0 * PI_D) * r_inner) * SIGMA_SB);", 1,
+     "tests/test_oracle_luminosity.py::test_eq18_inverts_the_inner_luminosity"),
 ]
 
 
