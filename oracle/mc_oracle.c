@@ -708,6 +708,9 @@ static void transport(const orc_model *m, const orc_geom *g, orc_rng *r, orc_rng
     }
 }
 
+/* Direct binning of an escaping packet (Sect. 2.9): lab energy into the bin
+ * of its lab frequency, bins uniform in nu over [nu_lo, nu_hi); below and
+ * above the range into the two extra tallies. */
 static void spectrum_add(const orc_model *m, double *spec, double nu_lab, double e_lab)
 {
     int B = m->spec_bins;
