@@ -173,3 +173,21 @@ def test_ionization_descriptor_matches_the_model():
     assert (a.ionization_mode, a.n_elements, a.n_stages) == (mc.MC_ION_SAHA, spec.n_elements, spec.n_stages)
     assert a.n_element == keep[-1].ctypes.data and keep[-1].shape == (4, spec.n_elements)
     assert a.delta == 1.0
+
+
+def test_model_calls_reject_a_null_model():
+    """Every per-model entry point answers a NULL handle with
+    MC_ERR_INVALID_ARG before touching the device (destroy is a no-op)."""
+    L = mc.load()
+    inv = mc.MC_ERR_INVALID_ARG
+    assert L.mc_set_plasma(None, None, None, None) == inv
+    assert L.mc_run_iteration(None, 1, 0, 10, 1e4) == inv
+    assert L.mc_run_iteration_range(None, 1, 0, 0, 10, 10, 1e4) == inv
+    assert L.mc_update_radiation_field(None, None, None) == inv
+    assert L.mc_read_estimators(None, None, None, None, None) == inv
+    assert L.mc_read_spectrum(None, None, None) == inv
+    assert L.mc_read_packets(None, 0, 1, None, None, None, None) == inv
+    assert L.mc_read_plasma(None, None, None, None) == inv
+    assert L.mc_read_ionization(None, None, None) == inv
+    assert L.mc_synchronize(None) == inv
+    L.mc_model_destroy(None)
