@@ -217,7 +217,8 @@ def run_reference(args):
             "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "sample_packets_per_step": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"first {sample} of 1e6 packets of iteration k, tau held from T_R=1e4 K"},
+                             "sample": f"first {sample} of 1e6 packets of iteration k, tau held from T_R=1e4 K",
+                             "note": "a packet sample: the iteration's longest random walks are not in it"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -244,6 +245,8 @@ def cpu_baseline_sample(spec, seconds_hint=10.0):
     st = r.stats
     return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"first {n} of the 1e6 packets of iteration 0 ({dt:.1f} s)",
+            "note": ("throughput over a packet sample: it leaves out the iteration's longest random walk "
+                     "(packet 126060, 94,495 segments), which the GPU step time includes"),
             "interactions_per_s": (st["line_interactions"] + st["e_scatters"]) / dt,
             "line_checks_per_s": st["line_checks"] / dt,
             "single_thread": {"value": n1 / dt1, "unit": UNIT,

@@ -465,7 +465,12 @@ mc_status mc_batch_autotune(mc_batch *b, const uint64_t *seeds, const uint32_t *
  *
  *  - The first call on a device does a one-time set-up on that device (it
  *    looks up the device address of the static array and fills the Planck
- *    table), so make that first call before any stream capture.
+ *    table), so make that first call before any stream capture: a first call
+ *    on a capturing stream is refused with MC_ERR_INVALID_ARG.  Device code
+ *    loads lazily, so that first call is also when the array and the
+ *    kernels' code are committed on the device; under a full memory budget it
+ *    can fail with MC_ERR_CUDA (later calls then retry the set-up).
+ *  - n_lines must be below 2^31 and spec_bins below 2^31 - 2.
  *  - Every call on a device shares the same static array, and the array keeps
  *    the last call's contents; the call clears what must start at zero
  *    (counters, and the j_est, nu_bar, j_blue and spectrum outputs).  Calls
@@ -505,6 +510,34 @@ typedef struct {
 } mc_noalloc_args;
 
 mc_status mc_transport_noalloc(const mc_noalloc_args *args, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Accuracy diagnostic of the device arithmetic.
+ *
+ * The transport kernels evaluate -ln z of a Sect. 2.6 optical-depth draw, the
+ * logarithm of the Sect. 2.4 Planck sampler, reciprocals of Doppler factors
+ * and frequencies (Sect. 2.5 frame transforms) and square roots of the
+ * shell-crossing and move geometry (Sect. 2.6) with their own device code,
+ * not with CUDA's functions.  mc_selftest_math evaluates one of them on the
+ * current device for n inputs, next to CUDA's counterpart:
+ *
+ *   fn = MC_MATH_NEG_LOG_U53: in = uint64_t u[n], 1 <= u <= 2^53;
+ *        ours = the kernels' -ln(u 2^-53), ref = -log(u 2^-53)
+ *   fn = MC_MATH_LOG:  in = double x[n] > 0 (normal); ours = log, ref = log(x)
+ *   fn = MC_MATH_RCP:  in = double x[n] (normal); ours = reciprocal, ref = 1.0 / x
+ *   fn = MC_MATH_SQRT: in = double x[n] >= 0 (0 or normal); ours = square root,
+ *        ref = sqrt(x) (IEEE, correctly rounded)
+ *
+ * `in`, `ours` and `ref` are HOST arrays of n elements (0 < n <= 2^28); the
+ * call allocates device memory, runs synchronously and frees it (a test
+ * utility, not for the transport path).  Returns MC_ERR_INVALID_ARG for an
+ * unknown fn, NULL buffers or a bad n, MC_ERR_CUDA (message in
+ * mc_last_error_message(NULL)) if a CUDA call fails. */
+#define MC_MATH_NEG_LOG_U53 0
+#define MC_MATH_LOG 1
+#define MC_MATH_RCP 2
+#define MC_MATH_SQRT 3
+mc_status mc_selftest_math(int32_t fn, const void *in, uint64_t n, double *ours, double *ref);
 
 /* Static description of a status code. */
 const char *mc_status_string(mc_status s);

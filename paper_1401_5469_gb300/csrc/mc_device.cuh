@@ -111,6 +111,24 @@ __device__ __forceinline__ double rcp64(double x) {
   return fma(r, e, r);
 }
 
+// Square root of x >= 0 (0 or a normal number) to within 1 ulp, in six
+// binary64 operations: y = rsqrt.approx.ftz.f64(x), t = x y, e = 1 - t y, and
+// sqrt(x) = sqrt(t / y) (1 + O(2^-53)) = t (1 - e)^(-1/2), taken from the
+// Taylor series t (1 + e/2 + 3e^2/8 + 5e^3/16) (the third-order Householder
+// step for 1/sqrt; J.-M. Muller, Elementary Functions, ch. 2).  |e| is about
+// twice the approximation's relative error, so the truncated e^4 term is far
+// below 2^-53.  (CUDA's sqrt rounds correctly but takes about ten binary64
+// instructions; on GB300 each costs its sub-partition's FP64 pipe ~64 cycles.)
+__device__ __forceinline__ double sqrt64(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double t = x * y;
+  const double e = fma(-t, y, 1.0);
+  const double p = fma(fma(0.3125, e, 0.375), e, 0.5);
+  const double r = fma(t * e, p, t);
+  return __double_as_longlong(x) == 0ll ? 0.0 : r;
+}
+
 // ln(2) split so that k * kLn2Head is exact for |k| < 2^20.
 constexpr double kLn2Head = 0x1.62e42fee00000p-1;
 constexpr double kLn2Tail = 0x1.a39ef35793c76p-33;

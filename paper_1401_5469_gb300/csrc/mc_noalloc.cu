@@ -36,6 +36,7 @@ constexpr size_t kShellOff = kPlanckOff + ((kPlanckLmax + 1) * sizeof(double) + 
 constexpr size_t kShellArrayBytes = MC_NOALLOC_MAX_SHELLS * sizeof(double);
 constexpr size_t kScratchBytes = kShellOff + 5 * kShellArrayBytes;
 static_assert(kScratchBytes <= 64 * 1024, "no-allocation scratch must stay at most 64 KiB");
+static_assert(kNCounterSlots * sizeof(unsigned long long) <= kPlanckOff, "counter slots overlap the Planck table");
 
 // The scratch itself: every GPU that loads the library holds these bytes
 // until the process exits.  Calls share it (see the header).
@@ -59,7 +60,10 @@ __global__ void noalloc_planck_kernel() {
   }
 }
 
-// Per call: zero the counters and derive the shell arrays from the caller's
+// Per call: zero every counter slot (run statistics, work counter and the
+// four flag words: deadline, queue-empty, last-warp and first-warp
+// timestamps, which this entry point does not read but clears all the same,
+// so that nothing of an earlier call survives in them) and derive the shell arrays from the caller's
 // velocities and electron densities (radii in units of c t_exp, their
 // inverses, and kappa' = sigma_T n_e c t_exp).
 __global__ void noalloc_prepare_kernel(int S, const double *v_inner, const double *v_outer,
@@ -71,7 +75,7 @@ __global__ void noalloc_prepare_kernel(int S, const double *v_inner, const doubl
   double *ixo = ixi + MC_NOALLOC_MAX_SHELLS;
   double *kap = ixo + MC_NOALLOC_MAX_SHELLS;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < kNStats + 2) cnt[t] = 0ull;
+  if (t < kNCounterSlots) cnt[t] = 0ull;
   if (t < S) {
     xi[t] = v_inner[t] / kC;
     xo[t] = v_outer[t] / kC;
@@ -98,6 +102,18 @@ mc_status scratch_for_current_device(cudaStream_t st, unsigned char **out) {
   if (dev < 0 || dev >= kMaxDevices) return reject("device index out of range");
   std::lock_guard<std::mutex> lk(g_setup_lock);
   if (!g_scratch_ptr[dev]) {
+    // The set-up kernel must run, not land in a graph that may never be
+    // launched: refuse a first call made while the stream is capturing.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) {
+      set_create_error(std::string("mc_transport_noalloc: cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+      return MC_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+      return reject("the first call on a device does its set-up and must not be made while the stream is capturing");
+    // Looking the array up loads this file's device code onto the device
+    // (modules load lazily), which is when the array's memory is committed.
     void *ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_scratch);
     if (e != cudaSuccess || !ptr) {
@@ -125,6 +141,8 @@ extern "C" mc_status mc_transport_noalloc(const mc_noalloc_args *a, void *stream
   if (S > MC_NOALLOC_MAX_SHELLS)
     return reject("n_shells exceeds MC_NOALLOC_MAX_SHELLS (" + std::to_string(MC_NOALLOC_MAX_SHELLS) + ")");
   if (L == 0) return reject("n_lines must be >= 1");
+  if (L > static_cast<uint32_t>(INT32_MAX)) return reject("n_lines must be below 2^31");
+  if (a->spec_bins > static_cast<uint32_t>(INT32_MAX) - 2u) return reject("spec_bins must be below 2^31 - 2");
   if (!a->v_inner || !a->v_outer || !a->n_e || !a->nu || !a->tau)
     return reject("geometry, line and tau buffers are required");
   if (!a->j_est || !a->nu_bar || !a->spectrum) return reject("j_est, nu_bar and spectrum outputs are required");

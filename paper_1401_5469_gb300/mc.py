@@ -46,9 +46,11 @@ EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_run_iter
             "mc_batch_read_timing", "mc_batch_last_error_message", "mc_batch_destroy",
             "mc_batch_set_launch", "mc_batch_get_launch", "mc_batch_autotune", "mc_batch_capture_graph",
             "mc_device_estimators", "mc_set_virtual_packets", "mc_read_virtual_spectrum",
-            "mc_t_inner_from_luminosity", "mc_emitted_luminosity", "mc_t_inner_update")
+            "mc_t_inner_from_luminosity", "mc_emitted_luminosity", "mc_t_inner_update",
+            "mc_selftest_math")
 
 MC_ORDER_PACKETS, MC_ORDER_WORK, MC_ORDER_GIVEN = 0, 1, 2
+MC_MATH_NEG_LOG_U53, MC_MATH_LOG, MC_MATH_RCP, MC_MATH_SQRT = 0, 1, 2, 3
 
 
 class mc_geometry_desc(C.Structure):
@@ -225,6 +227,8 @@ def load(build_if_missing: bool = True):
     L.mc_batch_capture_graph.argtypes = [vp, i32]
     L.mc_batch_autotune.restype = i32
     L.mc_batch_autotune.argtypes = [vp, vp, vp, vp, vp, P(mc_batch_launch), vp, vp]
+    L.mc_selftest_math.restype = i32
+    L.mc_selftest_math.argtypes = [i32, vp, u64, vp, vp]
     _lib = L
     return L
 
@@ -324,6 +328,17 @@ def mc_model_destroy(h):
 def mc_transport_noalloc(args, stream=None):
     """One transport launch on caller-owned device buffers; allocates nothing."""
     return _check(load().mc_transport_noalloc(C.byref(args), stream), None)
+
+
+def mc_selftest_math(fn, values):
+    """The kernels' own device arithmetic next to CUDA's (accuracy diagnostic):
+    returns (ours, ref) for the host input array ``values`` (uint64 draws for
+    MC_MATH_NEG_LOG_U53, binary64 otherwise)."""
+    dt = np.uint64 if fn == MC_MATH_NEG_LOG_U53 else np.float64
+    x = np.ascontiguousarray(values, dtype=dt)
+    ours, ref = np.empty(x.size), np.empty(x.size)
+    _check(load().mc_selftest_math(int(fn), _p(x), x.size, _p(ours), _p(ref)), None)
+    return ours, ref
 
 
 # ----------------------------------------------------------------- torch plumbing

@@ -191,3 +191,14 @@ def test_model_calls_reject_a_null_model():
     assert L.mc_read_ionization(None, None, None) == inv
     assert L.mc_synchronize(None) == inv
     L.mc_model_destroy(None)
+
+
+@pytest.mark.parametrize("field,value", [("n_lines", 2**31), ("spec_bins", 2**31 - 2), ("n_shells", 0)])
+def test_noalloc_rejects_out_of_range_sizes_before_device_work(field, value):
+    """mc_transport_noalloc checks its sizes on the host before any CUDA call
+    (counts that would not fit the kernels' signed 32-bit sizes included)."""
+    args = mc.mc_noalloc_args(n_shells=1, n_lines=1, spec_bins=10)
+    setattr(args, field, value)
+    with pytest.raises(mc.MCError) as ei:
+        mc.mc_transport_noalloc(args, None)
+    assert ei.value.code == mc.MC_ERR_INVALID_ARG

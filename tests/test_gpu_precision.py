@@ -9,6 +9,11 @@ oracle's seed must agree with the oracle far inside the noise (per-packet
 parity); the mixed run, which shares the oracle's draws, must differ from it
 by less than the noise.  (tests/precision_study.py runs the full study: 10
 iterations with the T_R/W update, a 4e6-packet final iteration, 16 seeds.)
+
+The binary64 statistic here is a noise-scale summary only; the parity claim
+for binary64 at this size is the element-by-element comparison with the
+oracle in test_gpu_fullsize_parity.py (every J, nu_bar, spectrum and J_blue
+element within 1e-9 relative).
 """
 import pytest
 
@@ -25,7 +30,7 @@ def report():
 
 
 @pytest.mark.parametrize("quantity", ["j_est", "nu_bar", "spectrum"])
-def test_binary64_matches_oracle_inside_the_noise(report, quantity):
+def test_binary64_oracle_difference_as_noise_statistic(report, quantity):
     r = report["iteration0"][quantity]["fp64_gpu_vs_oracle"]
     assert r["rms"] < 0.05, r
 

@@ -5,16 +5,23 @@ transport (a framework's fixed memory pool, a plug-in handed raw buffers, a
 loop that must not allocate).  They pass every buffer; the kernel's working
 memory is a static device array inside the library.  Here the caller's
 buffers come from torch, and two calls in a row (iterations 0 and 1) are
-checked against the model-based entry point (mc_run_iteration) with the
-tolerances of the parity tests: estimators and spectrum to 1e-9 relative,
-run statistics exactly.  The second call also shows that the shared scratch
-is cleared between calls.
+checked against the model-based entry point (mc_run_iteration) and against
+the oracle, with the tolerances of the parity tests: estimators and spectrum
+to 1e-9 relative, run statistics exactly.  The second call also shows that
+the shared scratch is cleared between calls, and that a call allocates
+nothing: torch's caching allocator, the device's default memory pool (its
+high-water mark reset before the call) and the device's free memory are the
+same after the call as before it.
 
 This file is named so that pytest collects it last.
 """
+import ctypes
+import os
+
 import numpy as np
 import pytest
 
+import oracle
 from paper_1401_5469_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -39,6 +46,35 @@ def _close(a, b, rtol):
 
 def _device(torch, a, dtype):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=dtype), device="cuda")
+
+
+class _DefaultPool:
+    """Usage counters of the current device's default memory pool (the pool
+    cudaMallocAsync draws from), read through the driver API."""
+
+    USED_CURRENT, USED_HIGH = 7, 8  # CU_MEMPOOL_ATTR_USED_MEM_CURRENT / _HIGH
+
+    def __init__(self, torch):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int(0)
+        assert self.cu.cuDeviceGet(ctypes.byref(dev), torch.cuda.current_device()) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def get(self, attr):
+        v = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        zero = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolSetAttribute(self.pool, self.USED_HIGH, ctypes.byref(zero)) == 0
+
+
+def _memory_state(torch):
+    torch.cuda.synchronize()
+    return {"reserved": torch.cuda.memory_reserved(), "allocated": torch.cuda.memory_allocated(),
+            "free": torch.cuda.mem_get_info()[0]}
 
 
 def _model_reference(mc, spec, tau, seed, iteration, n):
@@ -95,20 +131,39 @@ def test_noalloc_matches_model_entry_point_twice(env, kind):
         keep["j_blue"] = torch.empty(S * L, dtype=torch.float64, device="cuda")
         args.j_blue = keep["j_blue"].data_ptr()
     stream = torch.cuda.current_stream().cuda_stream
+    om = oracle.OracleModel(spec, tau=tau)
+    pool = _DefaultPool(torch)
     for iteration in (0, 1):
         args.iteration = iteration
+        if iteration == 1:  # the set-up happened in the first call: this one allocates nothing
+            before = _memory_state(torch)
+            used_before = pool.get(pool.USED_CURRENT)
+            pool.reset_high()
         mc.mc_transport_noalloc(args, stream)
         torch.cuda.synchronize()
+        if iteration == 1:
+            assert _memory_state(torch) == before
+            assert pool.get(pool.USED_CURRENT) == used_before
+            assert pool.get(pool.USED_HIGH) <= used_before
+        got = {k: keep[k].cpu().numpy() for k in ("j_est", "nu_bar", "spectrum", "stats")}
         j, nb, jb, sp, st = _model_reference(mc, spec, tau, spec.seed, iteration, n)
-        _close(keep["j_est"].cpu().numpy(), j, EST_RTOL)
-        _close(keep["nu_bar"].cpu().numpy(), nb, EST_RTOL)
-        _close(keep["spectrum"].cpu().numpy(), sp, EST_RTOL)
+        _close(got["j_est"], j, EST_RTOL)
+        _close(got["nu_bar"], nb, EST_RTOL)
+        _close(got["spectrum"], sp, EST_RTOL)
         if spec.j_blue:
             _close(keep["j_blue"].cpu().numpy().reshape(S, L), jb, EST_RTOL)
-        got = keep["stats"].cpu().numpy()
         want = [st[k] for k in ("escaped", "reabsorbed", "capped", "segments", "line_checks",
                                 "resonances", "line_interactions", "e_scatters", "shell_crossings")]
-        assert list(map(int, got)) == want
+        assert list(map(int, got["stats"])) == want
+        # and the oracle, on the same inputs and draws
+        r = oracle.run_iteration(om, spec.seed, iteration, n, spec.t_inner, threads=os.cpu_count() or 1,
+                                 record=False)
+        _close(got["j_est"], r.j_est, EST_RTOL)
+        _close(got["nu_bar"], r.nu_bar, EST_RTOL)
+        _close(got["spectrum"], r.spectrum, EST_RTOL)
+        if spec.j_blue:
+            _close(keep["j_blue"].cpu().numpy().reshape(S, L), r.j_blue, EST_RTOL)
+        assert list(map(int, got["stats"])) == [r.stats[k] for k in oracle.STAT_NAMES]
 
 
 def test_noalloc_rejects_too_many_shells(env):
