@@ -675,7 +675,15 @@ mc_status model_prepare(mc_model *m, cudaStream_t st, bool events) {
 }
 
 mc_status model_finish_transport(mc_model *m, const TransportParams &p, cudaStream_t st) {
-  if (!m->est_fix) return MC_OK;
+  if (!m->est_fix) {
+    if (!m->j_blue) return MC_OK;
+    // binary64: J_blue cells hold sums of E_lab / nu_lab^2; times nu_j
+    const cudaError_t e = launch_jblue_times_nu(m->j_blue, m->nu, static_cast<int>(m->S),
+                                                static_cast<int>(m->L), st);
+    if (e != cudaSuccess) return cuda_fail(m, e, "J_blue line factor");
+    m->launches += 1;
+    return MC_OK;
+  }
   cudaError_t e = launch_est_from_fix(m->est_fix, static_cast<int>(m->S), p.e_cmf, p.nu_scale,
                                       m->j_est, m->nu_bar, st);
   if (e != cudaSuccess) return cuda_fail(m, e, "estimator conversion");

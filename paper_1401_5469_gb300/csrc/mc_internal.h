@@ -183,6 +183,9 @@ cudaError_t launch_to_f32(const double *in, float *out, size_t n, cudaStream_t s
 // J_blue of a mixed launch is summed in the j_blue buffer as 64-bit fixed
 // point (units of 2^-32 E / nu_ref) and converted in place after the launch.
 cudaError_t launch_jblue_from_fix(double *j_blue, size_t n, double e_cmf, double inv_nu_ref, cudaStream_t st);
+// Binary64 J_blue: the transport sums E_lab / nu_lab^2 per (shell, line);
+// this multiplies every cell by its line frequency nu_j (Eq. 17).
+cudaError_t launch_jblue_times_nu(double *j_blue, const double *nu, int S, int L, cudaStream_t st);
 cudaError_t launch_est_from_fix(const unsigned long long *fix, int S, double e_cmf, double nu_ref,
                                 double *j_est, double *nu_bar, cudaStream_t st);
 cudaError_t launch_ionization(const IonParams &p, cudaStream_t st);  // two kernels

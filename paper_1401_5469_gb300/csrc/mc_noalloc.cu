@@ -222,6 +222,8 @@ extern "C" mc_status mc_transport_noalloc(const mc_noalloc_args *a, void *stream
   }
   e = launch_transport(p, a->line_mode, MC_PRECISION_FP64, a->j_blue != nullptr, false, nsm * bps,
                        transport_block_size(), st);
+  if (e == cudaSuccess && a->j_blue)  // cells hold sums of E_lab / nu_lab^2: times nu_j (Eq. 17)
+    e = launch_jblue_times_nu(a->j_blue, a->nu, static_cast<int>(S), static_cast<int>(L), st);
   if (e == cudaSuccess && a->stats)
     e = cudaMemcpyAsync(a->stats, cnt, kNStats * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) {

@@ -283,6 +283,21 @@ __global__ void jblue_from_fix_kernel(double *jb, size_t n, double e_cmf, double
     jb[i] = ((static_cast<double>(fix[i]) * (1.0 / kEstFixScale)) * e_cmf) * inv_nu_ref;
 }
 
+// Binary64 J_blue: the transport adds E_lab / nu_lab^2 at each Sobolev point
+// (the packet's weight, the same for every line of a flight segment); the
+// line's own factor nu_j of Eq. 17's E_lab nu_j / nu_lab^2 is applied here,
+// once per cell.  One thread per line, every shell: coalesced over lines.
+__global__ void jblue_times_nu_kernel(double *jb, const double *nu, int S, int L) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < L; j += stride) {
+    const double v = nu[j];
+    for (int s = 0; s < S; ++s) {
+      double *c = jb + static_cast<size_t>(s) * static_cast<size_t>(L) + j;
+      *c = *c * v;
+    }
+  }
+}
+
 __global__ void est_from_fix_kernel(const unsigned long long *fix, int S, double e_cmf, double nu_ref,
                                     double *j_est, double *nu_bar) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -375,6 +390,12 @@ cudaError_t launch_dbr_setup(uint32_t nnz, uint32_t n_rows, uint32_t L, int K,
 
 cudaError_t launch_jblue_from_fix(double *j_blue, size_t n, double e_cmf, double inv_nu_ref, cudaStream_t st) {
   jblue_from_fix_kernel<<<4 * 152, 256, 0, st>>>(j_blue, n, e_cmf, inv_nu_ref);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jblue_times_nu(double *j_blue, const double *nu, int S, int L, cudaStream_t st) {
+  const int blocks = (L + 255) / 256 < sm_count() * 8 ? (L + 255) / 256 : sm_count() * 8;
+  jblue_times_nu_kernel<<<blocks, 256, 0, st>>>(j_blue, nu, S, L);
   return cudaGetLastError();
 }
 

@@ -42,10 +42,17 @@ constexpr int kLineEvent = 1, kElectronEvent = 2, kShellEvent = 3;
 
 struct Packet {
   double p, q;               // x mu, x^2 - p^2
-  double nu_lab, e_lab, inv_nu, inv_D;
+  double nu_lab, e_lab, inv_nu;
+  // Frame quantities at the start of the next flight segment, carried from
+  // the event that began it (valid while have_cmf): D = 1 - p, 1/D, the
+  // comoving frequency nu_lab D and E_cmf D = E_lab D^2 (the estimators'
+  // weight per unit length).  After an interaction they are known without
+  // new products (nu_cmf is the emitted comoving frequency, E_cmf D = E_cmf' D
+  // with the new direction's D); after a shell crossing they are recomputed.
+  double D, inv_D, nu_cmf, eD2;
   int32_t shell, next_line;
   uint32_t pid;
-  bool have_inv_D;
+  bool have_cmf;
   uint32_t cnt[kNCounters];
 };
 
@@ -145,20 +152,71 @@ __device__ __forceinline__ double max0(double v) { return rawkey(v) > 0 ? v : 0.
 // x mu at the shell exit: +sqrt(x_out^2 - q), or -sqrt(x_in^2 - q) when the
 // ray meets the inner sphere.
 __device__ __forceinline__ double shell_exit(double q, bool inner, double xi2, double xo2) {
-  const double root = sqrt((inner ? xi2 : xo2) - q);
+  const double root = sqrt64((inner ? xi2 : xo2) - q);
   return inner ? -root : root;
 }
 
 // Does an event at path length l (units of c t_exp) come before the shell
-// exit?  Along the ray x mu grows by l and x^2 = q + (x mu)^2.  Outward exit:
-// before it exactly when x^2 < x_out^2 there (a point with x mu < 0 has
-// x^2 <= the current x^2).  Inner exit at x mu = -sqrt(x_in^2 - q): before
-// it exactly when x mu < 0 and x^2 > x_in^2 there.
-__device__ __forceinline__ bool inside_shell(double pp, double q, double l, bool inner, double xi2,
-                                             double xo2) {
-  const double pl = pp + l;
-  const long long k2 = rawkey(fma(pl, pl, q));  // all three squares are >= 0
+// exit?  Along the ray x mu grows by l and x^2 = q + (x mu)^2; pl = x mu and
+// r2 = x^2 at the event point.  Outward exit: before it exactly when x^2 <
+// x_out^2 there (a point with x mu < 0 has x^2 <= the current x^2).  Inner
+// exit at x mu = -sqrt(x_in^2 - q): before it exactly when x mu < 0 and
+// x^2 > x_in^2 there.
+__device__ __forceinline__ bool inside_shell(double pl, double r2, bool inner, double xi2, double xo2) {
+  const long long k2 = rawkey(r2);  // all three squares are >= 0
   return inner ? (strictly_negative(pl) && k2 > rawkey(xi2)) : k2 < rawkey(xo2);
+}
+
+// binary64 -> binary32 toward zero on the bit pattern (no conversion
+// instruction: on GB300 those issue on the binary64 pipe), for d >= 0 below
+// the binary32 overflow threshold; values below the binary32 normal range
+// give 0 (an absolute error under 2^-126).
+__device__ __forceinline__ float f32_rz(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const int e = static_cast<int>(b >> 52) - 1023 + 127;
+  return e <= 0 ? 0.0f : __int_as_float((e << 23) | static_cast<int>((b >> 29) & 0x7fffffull));
+}
+
+// Bit pattern of the binary64 value of a positive normal binary32 (exact).
+__device__ __forceinline__ long long f64_bits(float f) {
+  const unsigned int b = static_cast<unsigned int>(__float_as_int(f));
+  return static_cast<long long>(((static_cast<unsigned long long>(b >> 23) + (1023 - 127)) << 52) |
+                                (static_cast<unsigned long long>(b & 0x7fffffu) << 29));
+}
+
+// The comoving frequency at the shell exit, K = nu_lab (1 - p_exit) with
+// p_exit = +-sqrt64(x_b^2 - q) as shell_exit and the key below compute it
+// in binary64, bracketed from binary32 arithmetic: on success K lies in
+// [lo, hi] (binary64 bit patterns), so that a line frequency or threshold
+// outside the bracket is ordered against K without the binary64 root; a
+// value inside it needs the exact K.  Error budget (u = 2^-24): the
+// operands truncated to binary32 (2u each), the difference (u), the
+// approximate reciprocal square root (taken as 2^-20 relative), the
+// products and sums (u each), and the binary64 path's own rounding (1 ulp
+// root, 3 roundings); the bracket is widened by 2^-19 K beyond the sum so
+// that rounding its ends keeps K inside.  Near-tangent exits (x_b^2 - q
+// within 4x its own error) and roots of 0.5 or more are not bracketed.
+struct ShellBracket {
+  long long lo, hi;
+  bool ok;
+};
+__device__ __forceinline__ ShellBracket shell_bracket(double q, double xb2, bool inner, double nu_lab) {
+  ShellBracket b;
+  const float a = f32_rz(xb2), c = f32_rz(q), nu = f32_rz(nu_lab);
+  const float dq = a - c;
+  const float e1 = 0x1.0p-22f * (a + dq);  // >= |dq - (x_b^2 - q)| + the binary64 difference's rounding
+  b.ok = dq >= 4.0f * e1;
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(dq));
+  const float P = dq * r;                                  // ~ sqrt(x_b^2 - q)
+  const float ep = fmaf(0x1.0p-18f, P, 1.01f * (e1 * r));  // >= |p_exit| - P
+  b.ok = b.ok && P < 0.5f;
+  const float g = inner ? 1.0f + P : 1.0f - P;
+  const float k = nu * g;
+  const float ek = k * fmaf(2.5f, ep, 0x1.0p-19f);
+  b.lo = f64_bits(k - ek);
+  b.hi = f64_bits(k + ek);
+  return b;
 }
 
 // Injection at the inner boundary, Sect. 2.4: Planck-sampled comoving
@@ -182,8 +240,11 @@ __device__ __forceinline__ double inject(const TransportParams &p, const double 
   pk.nu_lab = nu_cmf * iD;
   pk.e_lab = p.e_cmf * iD;
   pk.inv_nu = rcp64(nu_cmf) * D;
+  pk.D = D;
   pk.inv_D = iD;
-  pk.have_inv_D = true;
+  pk.nu_cmf = nu_cmf;
+  pk.eD2 = p.e_cmf * D;
+  pk.have_cmf = true;
   pk.shell = 0;
   pk.next_line = first_redward(p.nu, p.L, nu_cmf);
 #pragma unroll
@@ -307,6 +368,32 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
   int32_t acc_s = -1;
   double acc_j = 0.0, acc_nb = 0.0;
   const long long *nub = reinterpret_cast<const long long *>(p.nu);
+  // the lane's current shell and its constants (reloaded on a shell change)
+  int32_t cs = -1;
+  double c_kap = 0.0, c_ikap = 0.0, c_xi2 = 0.0, c_xo2 = 0.0;
+  // Lines next_line and next_line + 1 of the next segment (frequency bits,
+  // Sobolev depth in the segment's shell, branching-row info), loaded by the
+  // event that began it as soon as next_line is known, so that their latency
+  // overlaps the event's arithmetic instead of opening the next scan.
+  bool lw_ok = false;
+  long long lw_b0 = 0, lw_b1 = 0;
+  double lw_t0 = 0.0, lw_t1 = 0.0;
+  unsigned long long lw_r0 = 0ull, lw_r1 = 0ull;
+  auto load_window = [&](int32_t s_, int32_t j_) {
+    const double *ts = p.tau + static_cast<size_t>(s_) * static_cast<size_t>(L);
+    lw_b0 = 0; lw_t0 = 0.0; lw_r0 = 0ull; lw_b1 = 0; lw_t1 = 0.0; lw_r1 = 0ull;
+    if (j_ < L) {
+      lw_b0 = __ldg(nub + j_);
+      lw_t0 = __ldg(ts + j_);
+      if (MODE >= 1 && p.row_info) lw_r0 = __ldg(p.row_info + j_);
+    }
+    if (j_ + 1 < L) {
+      lw_b1 = __ldg(nub + j_ + 1);
+      lw_t1 = __ldg(ts + j_ + 1);
+      if (MODE >= 1 && p.row_info) lw_r1 = __ldg(p.row_info + j_ + 1);
+    }
+    lw_ok = true;
+  };
 
   for (;;) {
     // ---- claim packets for idle lanes (one atomic per warp)
@@ -325,6 +412,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
           ds.init(p.key0, p.key1, pk.pid, p.iteration);
           const double nu_cmf0 = inject(p, p.planck_cdf, x0, x0sq, pk, ds);
           alive = true;
+          lw_ok = false;
           vdraws = 0u;
           if (p.n_virtual) {
             spawn_virtual(p, sh, VirtualLaunch{x0, x0sq, nu_cmf0, p.e_cmf, 0, pk.next_line, pk.pid, 0u, true});
@@ -367,68 +455,94 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       pk.cnt[0] += 1u;
       const int32_t s = pk.shell;
       const double pp = pk.p, q = pk.q, nu_lab = pk.nu_lab, inv_nu = pk.inv_nu;
-      // Doppler factor D = 1 - mu v/c, comoving frequency (Sect. 2.5)
-      const double D = 1.0 - pp;
-      const double inv_D = pk.have_inv_D ? pk.inv_D : rcp64(D);
-      const double nu_cmf = nu_lab * D;
-      const double eD2 = (pk.e_lab * D) * D;  // E_cmf D for the estimators
-      const double kap = s_kap[s];
-      const bool thomson = kap > 0.0;
+      if (!pk.have_cmf) {
+        // after a shell crossing: Doppler factor D = 1 - mu v/c at the boundary
+        // point, comoving frequency and E_cmf D (Sect. 2.5)
+        const double D0 = 1.0 - pp;
+        pk.D = D0;
+        pk.inv_D = rcp64(D0);
+        pk.nu_cmf = nu_lab * D0;
+        pk.eD2 = (pk.e_lab * D0) * D0;
+        pk.have_cmf = true;
+      }
+      const double D = pk.D, inv_D = pk.inv_D, nu_cmf = pk.nu_cmf, eD2 = pk.eD2;
+      if (s != cs) {
+        cs = s;
+        c_kap = s_kap[s];
+        c_ikap = s_ikap[s];
+        c_xi2 = s_xi2[s];
+        c_xo2 = s_xo2[s];
+      }
+      const bool thomson = rawkey(c_kap) > 0;
       // optical depth to the next event, tau = -ln z
       double tau_rem = wd.template next_tau<MODE == 2>(ds);
       // Shell boundary: at the exit point x mu = p_exit = +-sqrt(x_b^2 - q) (the
       // inner sphere is hit when moving inward with q <= x_in^2), so the path
       // length is p_exit - p and the comoving frequency there nu_lab (1 - p_exit).
-      const double xi2 = s_xi2[s], xo2 = s_xo2[s];
+      // That frequency orders the lines passed against the exit; it is first
+      // bracketed in binary32 (shell_bracket) and taken exactly (binary64
+      // root) only for a value inside the bracket or when the shell event
+      // wins.  An event at path length l with no line passed before it is
+      // placed against the exit through x^2 = q + (p+l)^2 at the event point,
+      // the same p + l and x^2 the move to the event computes.
+      const double xi2 = c_xi2, xo2 = c_xo2;
       const bool inner = strictly_negative(pp) && rawkey(q) <= rawkey(xi2);  // q, x_in^2 >= 0
-      // The root (one binary64 square root, ~650 cycles) is taken only when
-      // a line is passed or the shell event wins: an event at path length l
-      // lies inside the shell exactly when the radius there, x^2 = q + (p+l)^2,
-      // has not reached the exit sphere -- the same p + l and x^2 the move
-      // to the event computes anyway.
+      int shell_state = 0;  // 0 nothing known, 1 bracket [klo, khi], 2 exact (klo = khi = key)
+      long long klo = 0, khi = 0;
       double p_exit = 0.0;
-      long long key_shell = kKeyNegInf;
-      bool have_shell = false;
+      auto exact_exit = [&]() {
+        p_exit = shell_exit(q, inner, xi2, xo2);
+        klo = khi = rawkey(nu_lab * (1.0 - p_exit));  // > 0
+        shell_state = 2;
+      };
+      // is a Sobolev point or threshold at comoving frequency key beyond the exit?
+      auto beyond_exit = [&](long long key) -> bool {
+        if (key > khi) return false;
+        if (key > klo) exact_exit();
+        return key <= klo;
+      };
       double c_e = 0.0, thr_e = 0.0;
       long long key_e = kKeyNegInf;
       if (thomson) {
-        c_e = (nu_lab * s_ikap[s]) * inv_D;  // nu_lab / k, k = kappa' D
+        c_e = (nu_lab * c_ikap) * inv_D;  // nu_lab / k, k = kappa' D
         thr_e = fma(-tau_rem, c_e, nu_cmf);
         key_e = rawkey(thr_e);
       }
-      long long key_thr = key_e;  // the shell threshold joins once known
+      // J_blue weight of this segment, E_lab / nu_lab^2 (Eq. 17 without its
+      // line factor nu_j, applied per cell after the launch)
       const double e_inv2 = JB ? (pk.e_lab * inv_nu) * inv_nu : 0.0;
       const size_t row = static_cast<size_t>(s) * static_cast<size_t>(L);
       const double *tau_s = p.tau + row;
       int32_t j = pk.next_line;
       int kind = 0;
       double l = 0.0, nu_hit = 0.0;
+      double pl_ev = 0.0, r2_ev = 0.0;  // x mu and x^2 at the event, when the exit test made them
+      bool have_ev = false;
       unsigned long long rinfo_hit = 0ull;
       // two lines ahead are always in flight while line j is resolved
       long long bj = 0, bj_n = 0;
       double taul = 0.0, tau_n = 0.0;
       unsigned long long rinfo = 0ull, rinfo_n = 0ull;
-      if (j < L) {
-        bj = __ldg(nub + j);
-        taul = __ldg(tau_s + j);
-        if (MODE >= 1 && p.row_info) rinfo = __ldg(p.row_info + j);
-      }
-      if (j + 1 < L) {
-        bj_n = __ldg(nub + j + 1);
-        tau_n = __ldg(tau_s + j + 1);
-        if (MODE >= 1 && p.row_info) rinfo_n = __ldg(p.row_info + j + 1);
-      }
+      if (!lw_ok) load_window(s, j);
+      bj = lw_b0; taul = lw_t0; rinfo = lw_r0;
+      bj_n = lw_b1; tau_n = lw_t1; rinfo_n = lw_r1;
+      lw_ok = false;
+      long long bj_nn = 0;
+      double tau_nn = 0.0;
+      unsigned long long rinfo_nn = 0ull;
+      double D1_ev = 0.0;  // Doppler factor at the event point, when the scan made it
       while (j < L) {
         pk.cnt[1] += 1u;
-        long long bj_nn = 0;
-        double tau_nn = 0.0;
-        unsigned long long rinfo_nn = 0ull;
+        bj_nn = 0;
+        tau_nn = 0.0;
+        rinfo_nn = 0ull;
         if (j + 2 < L) {
           bj_nn = __ldg(nub + j + 2);
           tau_nn = __ldg(tau_s + j + 2);
           if (MODE >= 1 && p.row_info) rinfo_nn = __ldg(p.row_info + j + 2);
         }
-        if (bj <= key_thr) break;  // the Sobolev point lies beyond d_e (or the shell exit)
+        if (bj <= key_e) break;                             // the Sobolev point lies beyond d_e
+        if (shell_state != 0 && beyond_exit(bj)) break;     // ... or beyond the shell exit
         const double nuj = __longlong_as_double(bj);
         bool absorbed;
         double t = 0.0;
@@ -440,28 +554,39 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         }
         if (absorbed) {
           const double lj = max0(fma(-nuj, inv_nu, D));
-          if (!have_shell && !inside_shell(pp, q, lj, inner, xi2, xo2)) break;  // exit comes first
+          // the Sobolev point: nu_lab (1 - x mu) = nu_j, so x mu = 1 - nu_j / nu_lab
+          // and D = nu_j / nu_lab there (a resonance that rounding puts behind
+          // the packet is taken where the packet is)
+          const bool ahead = rawkey(lj) > 0;
+          pl_ev = ahead ? fma(-nuj, inv_nu, 1.0) : pp;
+          D1_ev = ahead ? nuj * inv_nu : D;
+          r2_ev = fma(pl_ev, pl_ev, q);
+          have_ev = true;
+          if (shell_state == 0 && !inside_shell(pl_ev, r2_ev, inner, xi2, xo2)) break;  // exit comes first
           pk.cnt[2] += 1u;
-          if (JB) atomicAdd(p.j_blue + row + j, nuj * e_inv2);
+          if (JB) atomicAdd(p.j_blue + row + j, e_inv2);
           kind = kLineEvent;
           l = lj;
           nu_hit = nuj;
           rinfo_hit = rinfo;
           break;
         }
-        if (!have_shell) {  // a line is passed: the scan needs the exit threshold
-          p_exit = shell_exit(q, inner, xi2, xo2);
-          key_shell = rawkey(nu_lab * (1.0 - p_exit));  // > 0
-          have_shell = true;
-          key_thr = key_shell > key_e ? key_shell : key_e;
-          if (bj <= key_shell) break;  // this line lies beyond the exit
+        if (shell_state == 0) {  // a line is passed: the scan needs the exit frequency
+          const ShellBracket sb = shell_bracket(q, inner ? xi2 : xo2, inner, nu_lab);
+          if (sb.ok) {
+            klo = sb.lo;
+            khi = sb.hi;
+            shell_state = 1;
+          } else {
+            exact_exit();
+          }
+          if (beyond_exit(bj)) break;  // this line lies beyond the exit
         }
         pk.cnt[2] += 1u;
-        if (JB) atomicAdd(p.j_blue + row + j, nuj * e_inv2);
+        if (JB) atomicAdd(p.j_blue + row + j, e_inv2);
         if (thomson) {
           thr_e = t;
           key_e = rawkey(t);
-          key_thr = key_shell > key_e ? key_shell : key_e;
         } else {
           tau_rem -= taul;
         }
@@ -470,16 +595,35 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         bj_n = bj_nn; tau_n = tau_nn; rinfo_n = rinfo_nn;
       }
       if (kind == 0) {
-        const double le = thomson ? max0(fma(-thr_e, inv_nu, D)) : 0.0;
-        const bool electron = have_shell ? key_e > key_shell
-                                         : thomson && inside_shell(pp, q, le, inner, xi2, xo2);
+        bool electron;
+        double le = 0.0;
+        have_ev = false;  // an absorbed line that lay beyond the exit left its point here
+        if (shell_state != 0) {
+          electron = thomson && !beyond_exit(key_e);
+          if (electron) le = max0(fma(-thr_e, inv_nu, D));
+        } else {
+          le = thomson ? max0(fma(-thr_e, inv_nu, D)) : 0.0;
+          if (thomson) {
+            pl_ev = pp + le;
+            r2_ev = fma(pl_ev, pl_ev, q);
+            have_ev = true;
+          }
+          electron = thomson && inside_shell(pl_ev, r2_ev, inner, xi2, xo2);
+        }
         if (electron) {
           kind = kElectronEvent;
           l = le;
+          if (!have_ev) {
+            pl_ev = pp + le;
+            r2_ev = fma(pl_ev, pl_ev, q);
+            have_ev = true;
+          }
+          D1_ev = 1.0 - pl_ev;
         } else {
-          if (!have_shell) p_exit = shell_exit(q, inner, xi2, xo2);
+          if (shell_state != 2) exact_exit();
           kind = kShellEvent;
           l = max0(p_exit - pp);
+          have_ev = false;
         }
       }
       // estimators, Eqs. 13-14 (segment-start comoving values)
@@ -500,15 +644,15 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         const int32_t ns = inner ? s - 1 : s + 1;
         pk.p = p_exit;
         pk.shell = ns;
-        pk.have_inv_D = false;
+        pk.have_cmf = false;
+        lw_ok = false;
         if (ns >= S) status = 1;
         else if (ns < 0) status = 2;
       } else {
-        // move to the event point: x mu becomes p + l, x^2 = q + (p + l)^2
-        const double pl = pp + l;
-        const double r2n = fma(pl, pl, q);
-        const double xn = sqrt(r2n);
-        const double D1 = 1.0 - pl;
+        // move to the event point (x mu, x^2 and D there from the scan)
+        const double r2n = r2_ev;
+        const double xn = sqrt64(r2n);
+        const double D1 = D1_ev;
         const double e_c = pk.e_lab * D1;
         double nu_c, inv_nu_c;
         if (kind == kLineEvent) {
@@ -521,15 +665,22 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
             nu_c = em.nu;
             inv_nu_c = em.inv_nu;
             pk.next_line = em.line + 1;
+            load_window(s, pk.next_line);
           } else {
             nu_c = nu_hit;
             inv_nu_c = rcp64(nu_hit);
             pk.next_line = j + 1;
+            lw_ok = true;  // lines j + 1, j + 2 are in the scan's registers
+            lw_b0 = bj_n; lw_t0 = tau_n; lw_r0 = rinfo_n;
+            lw_b1 = bj_nn; lw_t1 = tau_nn; lw_r1 = rinfo_nn;
           }
         } else {
           pk.cnt[4] += 1u;
           nu_c = nu_lab * D1;
           inv_nu_c = inv_nu * rcp64(D1);
+          lw_ok = true;  // the next segment starts at line j again
+          lw_b0 = bj; lw_t0 = taul; lw_r0 = rinfo;
+          lw_b1 = bj_n; lw_t1 = tau_n; lw_r1 = rinfo_n;
         }
         // isotropic re-emission: new direction, lab values from the comoving ones
         const double mu2 = DrawStream::mu_from_u53(wd.template next_u53<MODE == 2>(ds));
@@ -541,8 +692,11 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         pk.nu_lab = nu_c * iD2;
         pk.e_lab = e_c * iD2;
         pk.inv_nu = inv_nu_c * D2;
+        pk.D = D2;
         pk.inv_D = iD2;
-        pk.have_inv_D = true;
+        pk.nu_cmf = nu_c;       // = nu_lab D2
+        pk.eD2 = e_c * D2;      // = E_lab D2^2
+        pk.have_cmf = true;
         if (p.n_virtual) {
           spawn_virtual(p, sh, VirtualLaunch{xn, r2n, nu_c, e_c, s, pk.next_line, pk.pid, vdraws, false});
           vdraws += static_cast<uint32_t>(p.n_virtual);
