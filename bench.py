@@ -12,7 +12,10 @@ updated from the estimators.  The iteration index advances every step.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle (the plain
 FP64 C implementation used by the tests) on a bounded packet sample of the
-same workload.
+same workload.  The default line also carries the mixed-precision loop, the
+2000-line scatter model, and a ``batched`` object: the batched workload below
+(256 models, two groups, mixed precision) with its own roofline, and the
+per-model binary64 path on the first 8 of those models.
 
 ``--workload batched``: 256 ejecta models of uneven size (shells U{10..40},
 lines U{5e4..5e5}, packets log-uniform in [1e4, 1e6], velocities, epoch and
@@ -289,15 +292,25 @@ def run_ours(args):
     torch.cuda.set_device(local)
     spec = synth.downbranch_model()
     N = spec.n_packets
-    seed = spec.seed + 1000 * rank
+    seed = spec.seed
     m = mc.Model(spec)
     S, L = spec.n_shells, spec.n_lines
     m.set_plasma()  # T_R = 1e4 K, geometric W (Sect. 2.8)
     stream = torch.cuda.current_stream()
+    if ws > 1:
+        # one model iterated with ws x 1e6 packets per iteration: rank r transports
+        # the packet range shard.packet_range(r, ws, ws N), the ranks sum J, nu_bar,
+        # the spectrum and J_blue with one all-reduce each, and every rank applies
+        # the T_R/W update to the identical sums (Sect. 2.8)
+        from paper_1401_5469_gb300 import shard
 
-    def step(it):
-        m.run_iteration(seed, it, N, spec.t_inner)
-        mc.mc_update_radiation_field(m.h, None, None)
+        def step(it):
+            shard.run_sharded_iteration(m, seed, it, ws * N, spec.t_inner, j_blue=True, update=False)
+            mc.mc_update_radiation_field(m.h, None, None)
+    else:
+        def step(it):
+            m.run_iteration(seed, it, N, spec.t_inner)
+            mc.mc_update_radiation_field(m.h, None, None)
 
     # warm-up (W >= 3 enforced by the caller's arguments)
     it = 0
@@ -317,8 +330,7 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        m.run_iteration(seed, it, N, spec.t_inner)
-        mc.mc_update_radiation_field(m.h, None, None)
+        step(it)
         # per-kernel device times of this step (events on the model's stream)
         k_ms += m.timing()
         phase_ms += m.phases()
@@ -349,7 +361,10 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e_steps):
         mc.mc_set_plasma(m.h, t_h, w_h, None)
-        mc.mc_run_iteration(m.h, seed, it, N, spec.t_inner)
+        if ws > 1:
+            shard.run_sharded_iteration(m, seed, it, ws * N, spec.t_inner, j_blue=True, update=False)
+        else:
+            mc.mc_run_iteration(m.h, seed, it, N, spec.t_inner)
         mc.mc_read_estimators(m.h, j_h, nb_h, jb_h, None)
         mc.mc_read_spectrum(m.h, sp_h, None)
         mc.mc_update_radiation_field(m.h, t_h, w_h)
@@ -361,6 +376,20 @@ def run_ours(args):
     m.close()
     mixed = measure_mixed(spec, seed, args) if os.environ.get("BENCH_SKIP_MIXED") != "1" else None
     scatter = scatter_config(mc, synth) if rank == 0 else None
+    batched = None
+    if rank == 0 and ws == 1 and os.environ.get("BENCH_SKIP_BATCHED") != "1":
+        # the batched workload (256 uneven models x 10 iterations, mixed precision,
+        # one persistent launch per group iteration); per-model binary64 on the
+        # first 8 models for the ratio
+        r = measure_batched(256, 2, True, fp64_models=8, noise_models=0)
+        batched = {"metric": "models/s", "value": r["value"], "unit": "models/s",
+                   "wall_s": r["batched_s"], "config": r["config"], "packets_per_s": r["packets_per_s"],
+                   "segments_per_s": r["segments_per_s"], "interactions_per_s": r["interactions_per_s"],
+                   "groups": r["groups"], "launches": len(r["transport_ms_per_group_iteration"]),
+                   "roofline": r["roofline"], "autotune": r["autotune"],
+                   "fp64_per_model": r["fp64_per_model"],
+                   "speedup_vs_fp64_per_model": r["speedup_vs_fp64_per_model"],
+                   "clocks": r["clocks"]}
     if rank != 0:
         return 0
     ms_step = 1e3 * elapsed / args.steps
@@ -379,8 +408,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "shells": S, "lines": L, "packets_per_step": N,
+        "config": {"workload": WORKLOAD, "shells": S, "lines": L, "packets_per_step": ws * N,
                    "line_mode": "downbranch", "j_blue": True, "precision": "fp64",
+                   "parallelism": (f"packet ranges of one {ws}x1e6-packet iteration over {ws} GPUs, "
+                                   "estimators summed by all-reduce" if ws > 1 else "one GPU"),
                    "l2": "inputs larger than L2 (tau 80 MB + J_blue 80 MB rewritten every step)"},
         "interactions_per_s": ws * (per["line_interactions"] + per["e_scatters"]) / (ms_step * 1e-3),
         "line_checks_per_s": ws * per["line_checks"] / (ms_step * 1e-3),
@@ -397,6 +428,7 @@ def run_ours(args):
         "clocks": clk,
         "mixed_precision": mixed,
         "scatter_config": scatter,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -441,41 +473,45 @@ def _log(msg):
     print(f"[bench] {msg}", file=sys.stderr, flush=True)
 
 
-def run_batched(args):
-    """256 uneven models x 10 iterations: batched mixed vs per-model binary64."""
+def measure_batched(n_models=256, groups=2, j_blue=True, fp64_models=None, noise_models=16, n_it=10):
+    """256 uneven models x 10 iterations: batched mixed vs per-model binary64.
+
+    The per-model binary64 side runs the first ``fp64_models`` models of the
+    generated list (all of them by default) with the same seeds and packet
+    counts; ``noise_models`` of those are run again with another seed for the
+    Monte Carlo spread of T_R."""
     import torch
     from paper_1401_5469_gb300 import mc, synth
     torch.cuda.set_device(0)
-    n_models, n_it = args.models, 10
     t0 = time.perf_counter()
     specs = synth.batched_models(n_models=n_models, seed=1401, iterations=n_it)
-    _log(f"generated {n_models} models in {time.perf_counter() - t0:.1f} s")
+    gen_s = time.perf_counter() - t0
+    _log(f"generated {n_models} models in {gen_s:.1f} s")
     seeds = [5469 + k for k in range(n_models)]
     n = [s.n_packets for s in specs]
     t_in = [s.t_inner for s in specs]
     total_packets = int(sum(n))
-    stream = torch.cuda.current_stream()
 
     # ---- batched, mixed precision: G groups of models, one batch (persistent
     # launch, own stream) each; a group's next iteration is enqueued as soon as
     # its last one ends, so one group's bulk fills the SMs another's tail of
     # long random walks leaves idle (a model's results do not depend on its group)
-    jb = bool(args.j_blue)
-    G = max(1, min(args.groups, n_models))
+    jb = bool(j_blue)
+    G = max(1, min(groups, n_models))
     t0 = time.perf_counter()
     # deal models by work (packets x lines) round-robin, so the groups balance;
     # a group's models share one stream (the batch orders itself after it)
     by_work = sorted(range(n_models), key=lambda k: -n[k] * specs[k].n_lines)
-    groups = [by_work[g::G] for g in range(G)]
+    grp_of = [by_work[g::G] for g in range(G)]
     g_streams = [torch.cuda.Stream() for _ in range(G)]
-    group_of = {k: g for g, grp in enumerate(groups) for k in grp}
+    group_of = {k: g for g, grp in enumerate(grp_of) for k in grp}
     models = [mc.Model(s, precision=mc.MC_PRECISION_MIXED, j_blue=jb,
                        stream=ctypes.c_void_p(g_streams[group_of[k]].cuda_stream))
               for k, s in enumerate(specs)]
     for m in models:
         m.set_plasma()
-    batches = [mc.Batch([models[k] for k in grp]) for grp in groups]
-    gargs = [([seeds[k] for k in grp], [n[k] for k in grp], [t_in[k] for k in grp]) for grp in groups]
+    batches = [mc.Batch([models[k] for k in grp]) for grp in grp_of]
+    gargs = [([seeds[k] for k in grp], [n[k] for k in grp], [t_in[k] for k in grp]) for grp in grp_of]
     torch.cuda.synchronize()
     _log(f"created mixed models in {time.perf_counter() - t0:.1f} s ({G} groups)")
     t0 = time.perf_counter()
@@ -491,24 +527,33 @@ def run_batched(args):
     clocks.start()
     torch.cuda.synchronize()
     transport_ms = []
-    work = {"segments": 0, "line_checks": 0, "line_interactions": 0, "e_scatters": 0}
+    keys = ("segments", "line_checks", "resonances", "line_interactions", "e_scatters", "escaped")
+    work = {k: 0 for k in keys}
+    alg_bytes = 0.0
     w0 = time.perf_counter()
     for b, (sd, np_, ti) in zip(batches, gargs):
         b.run_iteration(sd, 0, np_, ti, update=True)
     for it in range(n_it):
         for g, (b, (sd, np_, ti)) in enumerate(zip(batches, gargs)):
             transport_ms.append(b.transport_ms())  # waits for this group's iteration
-            for k in groups[g]:  # per-model run statistics (read after the iteration)
+            gw = {k: 0 for k in keys}
+            for k in grp_of[g]:  # per-model run statistics (read after the iteration)
                 st = models[k].spectrum()[1]
-                for key in work:
-                    work[key] += st[key]
+                for key in keys:
+                    gw[key] += st[key]
+            for key in keys:
+                work[key] += gw[key]
+            # algorithmic bytes of this launch: nu per line check, binary32 tau and
+            # the 8-byte J_blue sum per Sobolev point, shell row + two estimator
+            # sums per segment, spectrum bin per escaping packet
+            alg_bytes += (8 * gw["line_checks"] + (4 + (8 if jb else 0)) * gw["resonances"]
+                          + 40 * gw["segments"] + 8 * gw["escaped"])
             if it + 1 < n_it:
                 b.run_iteration(sd, it + 1, np_, ti, update=True)
     for b in batches:
         b.synchronize()
     torch.cuda.synchronize()
     batched_s = time.perf_counter() - w0
-    wall_b = batched_s
     clk = clocks.stop()
     t_mixed = []
     for m in models:
@@ -521,7 +566,7 @@ def run_batched(args):
     _log(f"batched: {batched_s:.2f} s for {n_it} iterations")
 
     # ---- per-model binary64, the same models, seeds and packets
-    limit = int(os.environ.get("BENCH_FP64_MODELS", str(n_models)))
+    limit = n_models if fp64_models is None else min(int(fp64_models), n_models)
     fp64_s = 0.0
     t_fp64 = []
 
@@ -545,31 +590,38 @@ def run_batched(args):
     _log(f"per-model fp64: {fp64_s:.2f} s for {limit} models")
     # Monte Carlo noise of the same statistic: binary64 with another seed
     rms = lambda a, b_: float(np.sqrt(np.mean(((a - b_) / b_) ** 2)))
-    n_noise = min(16, limit)
+    n_noise = min(noise_models, limit)
     d_mix = [rms(t_mixed[k], t_fp64[k]) for k in range(limit)]
     d_seed = [rms(fp64_loop(specs[k], seeds[k] + 1_000_000), t_fp64[k]) for k in range(n_noise)]
     med = lambda v: float(np.median(v)) if v else None
     value = n_models / batched_s
-    line = {
-        "metric": "models/s", "value": value, "unit": "models/s", "n_gpus": 1, "steps": n_it,
-        "warmup": trials, "ms_per_step": 1e3 * batched_s / n_it, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+    peak, peak_kind = _peaks()
+    k_s = 1e-3 * sum(transport_ms)
+    return {
+        "value": value, "batched_s": batched_s,
         "config": {"workload": f"batched-{n_models}-uneven-models-10-iterations",
                    "models": n_models, "iterations": n_it, "packets_per_iteration": total_packets,
                    "shells": [min(s.n_shells for s in specs), max(s.n_shells for s in specs)],
                    "lines": [min(s.n_lines for s in specs), max(s.n_lines for s in specs)],
-                   "j_blue": jb, "line_mode": "downbranch",
+                   "j_blue": jb, "line_mode": "downbranch", "precision": "mixed",
                    "l2": "inputs larger than L2 (Sobolev depths and J_blue of all models)"},
         "packets_per_s": total_packets * n_it / batched_s,
         "segments_per_s": work["segments"] / batched_s,
         "line_checks_per_s": work["line_checks"] / batched_s,
         "interactions_per_s": (work["line_interactions"] + work["e_scatters"]) / batched_s,
         "segments_per_packet": work["segments"] / (total_packets * n_it),
-        "wall_s": wall_b,
         "groups": G,
         "transport_ms_per_group_iteration": transport_ms,
+        "roofline": {"bound": "hbm", "kernel": "transport_mixed (batched)",
+                     "achieved": alg_bytes / k_s / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg_bytes / k_s / 1e9 / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes": alg_bytes, "kernel_s": k_s,
+                     "aggregate_gbs_over_wall": alg_bytes / batched_s / 1e9,
+                     "note": "kernel_s sums the launches' CUDA-event durations; the two groups' "
+                             "launches overlap, so the aggregate over the wall clock is also given"},
         "autotune": {"launch": tuned, "transport_ms": tuned_ms, "trials": trials, "seconds": tune_s},
         "fp64_per_model": {"models_per_s": fp64_models_s, "seconds": fp64_s, "models_timed": limit,
+                           "which": f"the first {limit} of the {n_models} generated models (generation seed 1401)",
                            "packets_per_s": sum(n[:limit]) * n_it / fp64_s if limit else None,
                            "timing": "host clock around each model's 10 iterations (synchronised)"},
         "speedup_vs_fp64_per_model": value / fp64_models_s if limit else None,
@@ -579,7 +631,21 @@ def run_batched(args):
             "note": "per model, RMS over shells of the relative T_R difference; mixed and binary64 "
                     "share the seeds, but their histories part after rounding differences, so the "
                     "comparison is with the seed-to-seed Monte Carlo spread"},
+        "generation_s": gen_s,
         "clocks": clk,
+    }
+
+
+def run_batched(args):
+    """256 uneven models x 10 iterations: batched mixed vs per-model binary64."""
+    limit = int(os.environ.get("BENCH_FP64_MODELS", str(args.models)))
+    r = measure_batched(args.models, args.groups, bool(args.j_blue), fp64_models=limit)
+    value, batched_s = r.pop("value"), r.pop("batched_s")
+    line = {
+        "metric": "models/s", "value": value, "unit": "models/s", "n_gpus": 1, "steps": 10,
+        "warmup": r["autotune"]["trials"], "ms_per_step": 1e3 * batched_s / 10, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "wall_s": batched_s, **r,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -608,8 +674,9 @@ def run_serve(args):
                           n_iterations=int(rng.integers(5, 21)), seed=5469 + k, arrival=a)
             for k, a in enumerate(arrivals)]
     tick_packets = args.tick_packets or (25_000_000 if mixed else 5_000_000)
+    n_groups = max(1, args.serve_groups)
     server = serve.Server(hbm_budget_bytes=150e9, j_blue=False, precision=prec,
-                          max_tick_packets=tick_packets)
+                          max_tick_packets=tick_packets, n_groups=n_groups)
     clocks = ClockSampler(0)
     clocks.start()
     start = time.perf_counter()
@@ -627,7 +694,12 @@ def run_serve(args):
                 break
             time.sleep(max(0.0, min(reqs[nxt].arrival - now, 0.05)))
             continue
-        server.step(now)
+        if n_groups > 1:
+            # groups advance on their own streams; poll without waiting for the device
+            if server.poll(now) == 0:
+                time.sleep(0.0005)
+        else:
+            server.step(now)
         peak_resident = max(peak_resident, len(server.active))
     end = time.perf_counter() - start
     clk = clocks.stop()
@@ -651,7 +723,10 @@ def run_serve(args):
                    "arrival_rate": args.rate, "window_s": window_s, "warmup_s": warm_s,
                    "iterations": [5, 20], "hbm_budget_bytes": 150e9, "max_tick_packets": tick_packets,
                    "model_pool": "256 batched-workload models (seed 1401), one drawn per request",
-                   "j_blue": False},
+                   "j_blue": False, "groups": n_groups,
+                   "mode": ("groups of models on their own streams, each group's next iteration "
+                            "enqueued when its last ends" if n_groups > 1 else
+                            "ticks: every resident model advances by one iteration per tick")},
         "latency_s": lat,
         "requests": {"arrived_in_window": len(in_window), "finished_in_window": len(done),
                      "backlog_at_end": {"queued": backlog_queued, "resident": backlog_active}},
@@ -660,6 +735,8 @@ def run_serve(args):
         "tick_ms": {"p50": float(np.percentile(server.tick_ms, 50)) if server.tick_ms else None,
                     "max": float(np.max(server.tick_ms)) if server.tick_ms else None},
         "elapsed_s": end, "clocks": clk,
+        "host_s": server.host_s,
+        "admitted": sum(1 for r in reqs if r.admitted is not None),
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -789,6 +866,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--tick-packets", type=int, default=0)
+    ap.add_argument("--serve-groups", type=int, default=4,
+                    help="serving: model groups advancing independently (1 = one tick for all)")
     ap.add_argument("--j-blue", type=int, default=1, choices=[0, 1], help="J_blue estimators (batched workload)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -148,12 +148,18 @@ mc_status mc_batch_create(mc_model *const *models, uint32_t n_models, mc_batch *
   b->order.resize(n_models);
   std::iota(b->order.begin(), b->order.end(), 0u);
   for (uint32_t i = 0; i < n_models; ++i) b->models.push_back(models[i]);
+  // Stream-ordered device buffers and cached pinned host buffers: creating or
+  // destroying a batch does not synchronise the device, so batches of other
+  // models keep running on their own streams meanwhile.
   cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_params, n_models * sizeof(TransportParams));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_prefix, (n_models + 1) * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, kNCounterSlots * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMallocHost(&b->h_params, n_models * sizeof(TransportParams));
-  if (e == cudaSuccess) e = cudaMallocHost(&b->h_prefix, (n_models + 1) * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMallocAsync(&b->d_params, n_models * sizeof(TransportParams), b->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&b->d_prefix, (n_models + 1) * sizeof(unsigned long long), b->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&b->d_counters, kNCounterSlots * sizeof(unsigned long long), b->stream);
+  if (e == cudaSuccess) {
+    b->h_params = static_cast<TransportParams *>(pinned_get(n_models * sizeof(TransportParams), false));
+    b->h_prefix = static_cast<unsigned long long *>(pinned_get((n_models + 1) * sizeof(unsigned long long), false));
+    if (!b->h_params || !b->h_prefix) e = cudaErrorMemoryAllocation;
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreate(&b->t0);
@@ -388,11 +394,11 @@ void mc_batch_destroy(mc_batch *b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   for (mc_model *m : b->models) m->in_batch = false;
   drop_graph(b);
-  if (b->d_params) cudaFree(b->d_params);
-  if (b->d_prefix) cudaFree(b->d_prefix);
-  if (b->d_counters) cudaFree(b->d_counters);
-  if (b->h_params) cudaFreeHost(b->h_params);
-  if (b->h_prefix) cudaFreeHost(b->h_prefix);
+  if (b->d_params) cudaFreeAsync(b->d_params, b->stream);
+  if (b->d_prefix) cudaFreeAsync(b->d_prefix, b->stream);
+  if (b->d_counters) cudaFreeAsync(b->d_counters, b->stream);
+  pinned_put(b->h_params);
+  pinned_put(b->h_prefix);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->t0) cudaEventDestroy(b->t0);

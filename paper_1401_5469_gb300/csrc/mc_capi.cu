@@ -344,7 +344,7 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
     cudaStreamSynchronize(m->stream);
     free_all(m);
     cudaStreamSynchronize(m->stream);
-    if (m->cancel_host) cudaFreeHost(m->cancel_host);
+    pinned_put(m->cancel_host);
     for (int i = 0; i < kNEv; ++i) cudaEventDestroy(m->ev[i]);
     if (m->own_stream) cudaStreamDestroy(m->stream);
     delete m;
@@ -378,8 +378,9 @@ mc_status mc_model_create(const mc_geometry_desc *geom, const mc_line_desc *line
   }
   if (ok) ok = alloc_n(m, &m->n_e, S);
   if (ok) {  // the stop request: one pinned host word the kernels can read
-    void *h = nullptr, *d = nullptr;
-    ok = cudaHostAlloc(&h, sizeof(uint32_t), cudaHostAllocMapped) == cudaSuccess;
+    void *d = nullptr;
+    void *h = pinned_get(sizeof(uint32_t), true);
+    ok = h != nullptr;
     if (ok) {
       m->cancel_host = static_cast<uint32_t *>(h);
       *static_cast<volatile uint32_t *>(m->cancel_host) = 0u;
@@ -994,7 +995,7 @@ void mc_model_destroy(mc_model *m) {
   cudaStreamSynchronize(m->stream);
   free_all(m);
   cudaStreamSynchronize(m->stream);
-  if (m->cancel_host) cudaFreeHost(m->cancel_host);
+  pinned_put(m->cancel_host);
   for (int i = 0; i < kNEv; ++i) cudaEventDestroy(m->ev[i]);
   if (m->own_stream) cudaStreamDestroy(m->stream);
   delete m;

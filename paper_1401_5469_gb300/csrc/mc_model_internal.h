@@ -98,4 +98,10 @@ mc_status model_finish_transport(mc_model *m, const TransportParams &p, cudaStre
 // Eqs. 15-16 for this model on `st`; marks the Sobolev depths stale.
 mc_status model_update(mc_model *m, cudaStream_t st, bool events);
 
+// Pinned host blocks (mapped into the device's address space if `mapped`)
+// from a process-wide cache: no device-wide synchronisation once a block of
+// that size class has been allocated before.  nullptr if allocation fails.
+void *pinned_get(size_t bytes, bool mapped);
+void pinned_put(void *p);
+
 }  // namespace mcgpu

@@ -16,6 +16,14 @@ models (a captured CUDA graph).  In binary64 a tick launches every resident
 model's own iteration on the model's own stream, so that one model's long
 last random walks overlap the other models' work.
 
+Without ticks (``n_groups`` > 1, driven by ``poll``): the resident models are
+dealt into groups, each with its own CUDA stream and (in mixed precision) its
+own batched launch.  A group's next iteration is enqueued as soon as its
+previous one has ended, whatever the other groups are doing, so a model waits
+only for the slowest walk of its own group, and one group's bulk runs in
+another's tail.  Requests are admitted into a group when its iteration ends
+(or while it is empty), and only that group's batch is rebuilt.
+
 A request's results depend only on its own model, seed and iteration count:
 packet draws are keyed by (seed, iteration, packet), single and batched
 launches run the same kernel arithmetic, and in mixed precision J, nu_bar and
@@ -94,8 +102,11 @@ class Server:
     """
 
     def __init__(self, hbm_budget_bytes: float = 150e9, j_blue: bool = True, stream=None,
-                 precision: int = mc.MC_PRECISION_MIXED, max_tick_packets: Optional[int] = None):
+                 precision: int = mc.MC_PRECISION_MIXED, max_tick_packets: Optional[int] = None,
+                 n_groups: int = 1):
         self.budget = float(hbm_budget_bytes)
+        self.n_groups = int(n_groups)
+        self.groups: List[_Group] = []
         self.j_blue = j_blue
         self.stream = stream
         self.precision = precision
@@ -111,6 +122,9 @@ class Server:
         self.ticks = 0
         self.tick_ms: List[float] = []
         self.transport_ms: List[float] = []
+        # host seconds spent creating models, building batches and launching,
+        # and reading back results (without ticks)
+        self.host_s = {"admit": 0.0, "launch": 0.0, "complete": 0.0}
 
     # -- admission
     def submit(self, req: Request):
@@ -146,6 +160,18 @@ class Server:
                 return True
         if rid not in self.active:
             return False
+        for g in self.groups:  # without ticks: wait for the request's group to end its iteration
+            if rid in g.ids:
+                if g.event is not None:
+                    g.event.synchronize()
+                    self._complete_group(g, time.perf_counter())
+                    if rid not in self.active:  # it finished with that iteration
+                        return True
+                if g.batch is not None:
+                    g.batch.close()
+                    g.batch, g.batch_ids = None, []
+                g.ids.remove(rid)
+                g.packets -= self.active[rid][0].spec.n_packets
         if self.batch is not None:
             self.batch.close()  # the batch goes before its models
             self.batch = None
@@ -218,12 +244,139 @@ class Server:
             self._retire(rid, end)
         return len(reqs)
 
+    # -- without ticks: groups of models advancing on their own streams
+    def poll(self, now: float) -> int:
+        """Advance every group whose last iteration has ended: count the
+        iteration for its models, retire the finished ones, admit waiting
+        requests into it and enqueue its next iteration.  Never waits for the
+        device.  Returns the number of model iterations completed."""
+        if not self.groups:
+            self.groups = [_Group(_new_stream()) for _ in range(max(1, self.n_groups))]
+        completed = 0
+        for g in self.groups:
+            if g.event is not None:
+                if not g.event.query():
+                    continue
+                g.event = None
+                t0 = time.perf_counter()
+                completed += self._complete_group(g, now)
+                self.host_s["complete"] += time.perf_counter() - t0
+            t0 = time.perf_counter()
+            self._admit_group(g, now)
+            t1 = time.perf_counter()
+            if g.ids:
+                self._launch_group(g)
+            self.host_s["admit"] += t1 - t0
+            self.host_s["launch"] += time.perf_counter() - t1
+        return completed
+
+    def _complete_group(self, g, now: float) -> int:
+        if g.batch is not None:
+            g.transport_ms.append(g.batch.transport_ms())
+        self.tick_ms.append(1e3 * (time.perf_counter() - g.t_launch))
+        self.ticks += 1
+        finished = []
+        for rid in g.ids:
+            r, m, _ = self.active[rid]
+            r.done_iterations += 1
+            if r.keep_history:
+                j, nb, _, _ = m.estimators()
+                r.history.append((j, nb) + _radiation_field(m))
+            if r.done_iterations >= r.n_iterations:
+                r.j_est, r.nu_bar, _, _ = m.estimators()
+                r.spectrum = m.spectrum()[0]
+                r.t_rad, r.w = _radiation_field(m)
+                finished.append(rid)
+        if finished and g.batch is not None:
+            g.batch.close()  # the batch goes before its models
+            g.batch, g.batch_ids = None, []
+        for rid in finished:
+            g.ids.remove(rid)
+            g.packets -= self.active[rid][0].spec.n_packets
+            self._retire(rid, now)
+        return len(g.ids) + len(finished)
+
+    def _admit_group(self, g, now: float):
+        cap = None if self.max_tick_packets is None else self.max_tick_packets / len(self.groups)
+        while self.queue:
+            req = self.queue[0]
+            need = model_footprint_bytes(req.spec, self.j_blue, self.precision)
+            if self.active and self.used + need > self.budget:
+                break
+            if g.ids and cap is not None and g.packets + req.spec.n_packets > cap:
+                break
+            self.queue.popleft()
+            m = mc.Model(req.spec, precision=self.precision, j_blue=self.j_blue,
+                         stream=g.stream_handle())
+            m.set_plasma()
+            req.admitted = now
+            self.active[req.rid] = (req, m, need)
+            self.used += need
+            self.tick_packets += req.spec.n_packets
+            g.ids.append(req.rid)
+            g.packets += req.spec.n_packets
+
+    def _launch_group(self, g):
+        reqs = [self.active[r][0] for r in g.ids]
+        models = [self.active[r][1] for r in g.ids]
+        g.t_launch = time.perf_counter()
+        if self.precision == mc.MC_PRECISION_MIXED:
+            if g.ids != g.batch_ids:
+                if g.batch is not None:
+                    g.batch.close()
+                g.batch = mc.Batch(models)
+                g.batch_ids = list(g.ids)
+            g.batch.run_iteration([r.seed for r in reqs], [r.done_iterations for r in reqs],
+                                  [r.spec.n_packets for r in reqs], [r.spec.t_inner for r in reqs],
+                                  update=True)
+        else:
+            for r, m in zip(reqs, models):  # in order on the group's stream
+                m.run_iteration(r.seed, r.done_iterations, r.spec.n_packets, r.spec.t_inner)
+                mc.mc_update_radiation_field(m.h, None, None)
+        g.event = _new_event()
+        g.event.record(g.stream)
+
     def close(self):
         if self.batch is not None:
             self.batch.close()
             self.batch = None
+        for g in self.groups:
+            if g.event is not None:
+                g.event.synchronize()
+            if g.batch is not None:
+                g.batch.close()
+                g.batch = None
+            g.ids = []
         for rid in list(self.active):
             self._retire(rid, time.perf_counter())
+
+
+def _new_stream():
+    import torch
+    return torch.cuda.Stream()
+
+
+def _new_event():
+    import torch
+    return torch.cuda.Event()
+
+
+class _Group:
+    """A group of resident models sharing one CUDA stream and one batch."""
+
+    def __init__(self, stream):
+        self.stream = stream
+        self.ids: List[int] = []
+        self.batch: Optional[mc.Batch] = None
+        self.batch_ids: List[int] = []
+        self.event = None
+        self.t_launch = 0.0
+        self.packets = 0
+        self.transport_ms: List[float] = []
+
+    def stream_handle(self):
+        import ctypes
+        return ctypes.c_void_p(getattr(self.stream, "cuda_stream", 0))
 
 
 def _radiation_field(m):

@@ -63,3 +63,41 @@ def test_requests_same_alone_and_in_the_mix(env):
         m.close()
     lat = serve.percentiles([r.latency for r in reqs])
     assert lat["p50"] is not None and lat["p99"] >= lat["p50"]
+
+
+def test_grouped_service_same_alone_and_in_the_mix(env):
+    """Without ticks: two groups of models on their own streams, each group's
+    next iteration enqueued as soon as its last one ends; requests join a
+    group when its iteration ends.  Every request's per-iteration J, nu_bar,
+    T_R and W equal, bit for bit, the model iterated alone."""
+    mc, serve = env
+    sizes = [(14, 4000, 1500, 3), (20, 9000, 3000, 2), (10, 2500, 800, 4), (25, 6000, 2000, 2),
+             (16, 3000, 1200, 3)]
+    specs = [synth.downbranch_model(n_lines=L, n_shells=S, n_packets=N, seed=1600 + k,
+                                    t_inner=9000.0 + 300 * k)
+             for k, (S, L, N, _) in enumerate(sizes)]
+    reqs = [serve.Request(rid=k, spec=specs[k], n_iterations=sizes[k][3], seed=91 + k, keep_history=True)
+            for k in range(len(specs))]
+    server = serve.Server(hbm_budget_bytes=1e12, n_groups=2, max_tick_packets=8000)
+    import time
+    polls, t_end = 0, time.perf_counter() + 120.0
+    while time.perf_counter() < t_end and len(server.done) < len(reqs):
+        if polls < len(reqs):
+            server.submit(reqs[polls])
+        if server.poll(float(polls)) == 0:
+            time.sleep(0.001)
+        polls += 1
+    server.close()
+    assert len(server.done) == len(reqs)
+    for r in reqs:
+        assert len(r.history) == r.n_iterations
+        m = mc.Model(r.spec, precision=mc.MC_PRECISION_MIXED)
+        m.set_plasma()
+        for it in range(r.n_iterations):
+            m.run_iteration(r.seed, it, r.spec.n_packets, r.spec.t_inner)
+            j, nb, _, _ = m.estimators()
+            t, w = m.update_radiation_field()
+            j_s, nb_s, t_s, w_s = r.history[it]
+            assert np.array_equal(j_s, j) and np.array_equal(nb_s, nb), (r.rid, it)
+            assert np.array_equal(t_s, t) and np.array_equal(w_s, w), (r.rid, it)
+        m.close()

@@ -116,3 +116,42 @@ def test_sharded_iteration_over_one_process_group(mc):
             b.close()
     finally:
         dist.destroy_process_group()
+
+
+def test_two_packet_ranges_sum_to_the_oracle_iteration(mc):
+    """The full-size downbranch iteration (500,000 lines, 1e6 packets, J_blue)
+    split into two packet ranges as two ranks would run them (one after the
+    other on this GPU): the summed J, nu_bar, spectrum and every J_blue cell
+    equal the oracle's whole iteration within 1e-9 relative, and each range's
+    run statistics add up to the oracle's."""
+    import oracle
+    spec = synth.downbranch_model()
+    n, S, L = spec.n_packets, spec.n_shells, spec.n_lines
+    t_rad = np.full(S, 1.0e4)
+    tau = oracle.plasma_tau(spec, t_rad, oracle.geometric_dilution(spec))
+    sums = {"j": 0.0, "nb": 0.0, "jb": 0.0, "sp": 0.0}
+    stats = {}
+    for rank in range(2):
+        first, count = shard.packet_range(rank, 2, n)
+        m = mc.Model(spec)
+        m.set_plasma(tau=tau)
+        m.run_iteration_range(spec.seed, 0, first, count, n, spec.t_inner)
+        j, nb, jb, _ = m.estimators(j_blue=True)
+        sp, st, _ = m.spectrum()
+        m.close()
+        sums["j"] = sums["j"] + j
+        sums["nb"] = sums["nb"] + nb
+        sums["jb"] = sums["jb"] + jb.reshape(S, L)
+        sums["sp"] = sums["sp"] + sp
+        for k, v in st.items():
+            stats[k] = stats.get(k, 0) + v
+    r = oracle.run_iteration(oracle.OracleModel(spec, tau=tau), spec.seed, 0, n, spec.t_inner,
+                             threads=os.cpu_count() or 1, record=False)
+    for k in oracle.STAT_NAMES:
+        assert stats[k] == r.stats[k], k
+    for name, a, b in (("J", sums["j"], r.j_est), ("nu_bar", sums["nb"], r.nu_bar),
+                       ("spectrum", sums["sp"], r.spectrum), ("J_blue", sums["jb"], r.j_blue)):
+        zero = b == 0
+        assert np.all(a[zero] == 0), name
+        rel = np.abs(a[~zero] - b[~zero]) / np.abs(b[~zero])
+        assert rel.max() <= 1e-9, (name, float(rel.max()))

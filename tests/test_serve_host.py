@@ -196,3 +196,86 @@ def test_withdrawn_requests_release_their_resources(fake):
     assert sorted(r.rid for r in srv.done) == [0, 2]
     assert all(r.done_iterations == 3 for r in srv.done)
     assert srv.used == 0 and srv.tick_packets == 0 and _FakeModel.live == 0
+
+
+class _FakeEvent:
+    """Completes after a set number of polls of its group (the device time)."""
+    duration = {}
+
+    def __init__(self):
+        self.left = None
+
+    def record(self, stream):
+        self.stream = stream
+        self.left = _FakeEvent.duration.get(stream.name, 1)
+
+    def query(self):
+        self.left -= 1
+        return self.left <= 0
+
+    def synchronize(self):
+        self.left = 0
+
+
+class _FakeStream:
+    count = 0
+
+    def __init__(self):
+        self.name = _FakeStream.count
+        _FakeStream.count += 1
+
+
+@pytest.fixture
+def grouped(fake, monkeypatch):
+    _FakeStream.count = 0
+    _FakeEvent.duration = {}
+    monkeypatch.setattr(serve, "_new_stream", _FakeStream)
+    monkeypatch.setattr(serve, "_new_event", _FakeEvent)
+    return serve
+
+
+def test_groups_advance_independently(grouped):
+    """Without ticks: a group whose iterations take long (stream 0, 5 polls
+    each) does not hold back the other group (stream 1, 1 poll each); every
+    model still runs iterations 0 .. n-1 with its own seed, exactly once."""
+    _FakeEvent.duration = {0: 5, 1: 1}
+    specs = [_spec(300, 100 + k) for k in range(4)]
+    srv = serve.Server(hbm_budget_bytes=1e12, n_groups=2, max_tick_packets=250)
+    reqs = [serve.Request(rid=k, spec=s, n_iterations=3, seed=10 + k) for k, s in enumerate(specs)]
+    for r in reqs:
+        srv.submit(r)
+    polls = 0
+    finished_at = {}
+    while (srv.queue or srv.active) and polls < 200:
+        srv.poll(float(polls))
+        for r in srv.done:
+            finished_at.setdefault(r.rid, polls)
+        polls += 1
+    srv.close()
+    assert sorted(r.rid for r in srv.done) == [0, 1, 2, 3]
+    # the packet cap (125 per group) puts one model in each group at a time:
+    # rids 0 and 1 start together; rid 1 (fast group) finishes and rids 2, 3
+    # follow it in the fast group while rid 0 is still in the slow one
+    assert finished_at[1] < finished_at[0] and finished_at[2] < finished_at[0]
+    seen = {}
+    for b in _FakeBatch.created:
+        for m in b.models:
+            seen.setdefault(id(m), m)
+    runs = sorted((m.spec.n_packets, m.iterations) for m in seen.values())
+    assert runs == [(100 + k, [(10 + k, 0), (10 + k, 1), (10 + k, 2)]) for k in range(4)]
+    assert _FakeModel.live == 0 and srv.used == 0
+
+
+def test_grouped_withdraw_waits_for_the_group(grouped):
+    _FakeEvent.duration = {0: 3, 1: 3}
+    specs = [_spec(300, 100 + k) for k in range(2)]
+    srv = serve.Server(hbm_budget_bytes=1e12, n_groups=2, max_tick_packets=250)
+    for k, s in enumerate(specs):
+        srv.submit(serve.Request(rid=k, spec=s, n_iterations=5, seed=k))
+    srv.poll(0.0)
+    assert sorted(srv.active) == [0, 1]
+    assert srv.withdraw(0)      # its group's iteration in flight: it ends first, then the model goes
+    assert 0 not in srv.active and srv.aborted[-1].rid == 0
+    while srv.active:
+        srv.poll(1.0)
+    assert [r.rid for r in srv.done] == [1] and _FakeModel.live == 0
