@@ -262,6 +262,23 @@ struct WarpDraws {
     base = b;
     pid = pk;
   }
+  // Lone-walker mode (every lane of the warp holds the walker's draw stream):
+  // refill when fewer than the three draws a segment may take are left.
+  __device__ __forceinline__ void keep(const DrawStream &ds, uint32_t k0, uint32_t k1, uint32_t iteration,
+                                       unsigned lane) {
+    if (ds.packet == pid && ds.d + 3u <= base + kWarpDraws) return;
+    const uint32_t b = ds.d & ~1u;
+    const uint4 o = philox4x32_10(make_uint4((b >> 1) + lane, ds.packet, iteration, 0u), k0, k1);
+    const unsigned long long u0 = DrawStream::u53_of(o.x, o.y), u1 = DrawStream::u53_of(o.z, o.w);
+    __syncwarp();  // every lane has read the old contents
+    u[2 * lane] = u0;
+    u[2 * lane + 1] = u1;
+    t[2 * lane] = neg_log_u53(u0 + 1ull);
+    t[2 * lane + 1] = neg_log_u53(u1 + 1ull);
+    __syncwarp();
+    base = b;
+    pid = ds.packet;
+  }
   // The live lane's next draw (u53, or the -ln z of an open-interval draw).
   // UNBOUNDED: a segment may take more draws than the buffer holds (a macro
   // atom's internal jumps), and past its end a draw is computed on its own;

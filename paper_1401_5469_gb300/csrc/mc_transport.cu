@@ -78,30 +78,50 @@ struct Emission {
 // upper level's branching row with z < cdf[k], z = u 2^-53.  With the guide
 // table: z < cdf[k] <=> u < ceil(cdf[k] 2^53) = thr[k] exactly; the search
 // starts at the guide entry of bucket floor(z n) and walks forward.
+// The bucket slot of draw u in the branching row of rinfo (begin | length << 32).
+__device__ __forceinline__ const DbrRec *bucket_slot(const TransportParams &p, unsigned long long rinfo,
+                                                     unsigned long long u) {
+  const uint32_t b = static_cast<uint32_t>(rinfo), len = static_cast<uint32_t>(rinfo >> 32);
+  const uint32_t bucket = static_cast<uint32_t>(__umul64hi(u << 11, static_cast<unsigned long long>(len)));
+  return p.dbr_bucket + b + bucket;
+}
+
+// A slot record as two 16-byte halves: {thr, nu} and {inv_nu, emit | guide << 32}.
+__device__ __forceinline__ void load_slot(const DbrRec *slot, ulonglong2 &a, ulonglong2 &c) {
+  a = __ldg(reinterpret_cast<const ulonglong2 *>(slot));
+  c = __ldg(reinterpret_cast<const ulonglong2 *>(slot) + 1);
+}
+
+// The emission from a loaded slot record: the slot itself when u is below its
+// threshold, else the walk forward from its guide entry.
+__device__ __forceinline__ Emission pick_from_slot(const TransportParams &p, unsigned long long rinfo,
+                                                   unsigned long long u, ulonglong2 a, ulonglong2 c) {
+  Emission em;
+  if (u < a.x) {
+    em.nu = __longlong_as_double(static_cast<long long>(a.y));
+    em.inv_nu = __longlong_as_double(static_cast<long long>(c.x));
+    em.line = static_cast<int32_t>(static_cast<uint32_t>(c.y));
+    return em;
+  }
+  const DbrRec *rec = p.dbr_rec;
+  uint32_t i = static_cast<uint32_t>(rinfo) + static_cast<uint32_t>(c.y >> 32) + 1u;
+  unsigned long long thr = __ldg(&rec[i].thr);
+  while (u >= thr) { ++i; thr = __ldg(&rec[i].thr); }
+  em.nu = __ldg(&rec[i].nu);
+  em.inv_nu = __ldg(&rec[i].inv_nu);
+  em.line = static_cast<int32_t>(__ldg(&rec[i].emit));
+  return em;
+}
+
 __device__ __forceinline__ Emission downbranch_pick(const TransportParams &p, int32_t j,
                                                     unsigned long long rinfo, unsigned long long u) {
   Emission em;
   if (p.dbr_rec) {
     // bucket slot: a copy of the guide entry's record, so that the common case
-    // (the guide entry is the answer) is a single 32-byte load
-    const uint32_t b = static_cast<uint32_t>(rinfo), len = static_cast<uint32_t>(rinfo >> 32);
-    const uint32_t bucket = static_cast<uint32_t>(__umul64hi(u << 11, static_cast<unsigned long long>(len)));
-    const DbrRec *slot = p.dbr_bucket + b + bucket;
-    unsigned long long thr = __ldg(&slot->thr);
-    if (u < thr) {
-      em.nu = __ldg(&slot->nu);
-      em.inv_nu = __ldg(&slot->inv_nu);
-      em.line = static_cast<int32_t>(__ldg(&slot->emit));
-      return em;
-    }
-    const DbrRec *rec = p.dbr_rec;
-    uint32_t i = b + __ldg(&slot->guide) + 1u;
-    thr = __ldg(&rec[i].thr);
-    while (u >= thr) { ++i; thr = __ldg(&rec[i].thr); }
-    em.nu = __ldg(&rec[i].nu);
-    em.inv_nu = __ldg(&rec[i].inv_nu);
-    em.line = static_cast<int32_t>(__ldg(&rec[i].emit));
-    return em;
+    // (the guide entry is the answer) is one 32-byte record load
+    ulonglong2 a, c;
+    load_slot(bucket_slot(p, rinfo, u), a, c);
+    return pick_from_slot(p, rinfo, u, a, c);
   }
   const int32_t row = __ldg(p.line_row + j);
   uint32_t lo = __ldg(p.dbr_offset + row), hi = __ldg(p.dbr_offset + row + 1) - 1u;
@@ -362,6 +382,20 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
   wd.init(reinterpret_cast<unsigned long long *>(sh + kShellArrays * S) +
           2 * kWarpDraws * (threadIdx.x >> 5));
   bool alive = false, finished = false;
+  // Lone-walker mode: once the packet queue is empty and a warp is down to
+  // one live walk, every lane of the warp takes that walk's state and runs
+  // its segments together with the owner lane (the same instructions on the
+  // same values, so the walk's results are those of the owner alone).  The
+  // lanes then load the line list 32 lines at a time in one coalesced load
+  // (line lwin_j0 + lane in each lane) and pass line data by shuffles;
+  // only the owner lane makes the walk's side effects (estimator and J_blue
+  // atomics, spectrum, records, statistics).
+  bool lone = false;
+  int owner = 0;
+  int32_t lwin_j0 = 0, lwin_s = -1;
+  long long lwin_b = 0;
+  double lwin_t = 0.0;
+  unsigned long long lwin_r = 0ull;
   uint32_t vdraws = 0u;  // v-packet draws used by this lane's packet
   unsigned long long n_esc = 0, n_reab = 0, n_cap = 0, n_seg = 0, n_chk = 0, n_res = 0, n_lint = 0,
                      n_esca = 0, n_shell = 0;
@@ -393,6 +427,29 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       if (MODE >= 1 && p.row_info) lw_r1 = __ldg(p.row_info + j_ + 1);
     }
     lw_ok = true;
+  };
+  auto lone_reload = [&](int32_t s_, int32_t j0) {
+    lwin_j0 = j0;
+    lwin_s = s_;
+    const int32_t jj = j0 + static_cast<int32_t>(lane);
+    lwin_b = 0;
+    lwin_t = 0.0;
+    lwin_r = 0ull;
+    if (jj < L) {
+      lwin_b = __ldg(nub + jj);
+      lwin_t = __ldg(p.tau + static_cast<size_t>(s_) * static_cast<size_t>(L) + jj);
+      if (MODE >= 1 && p.row_info) lwin_r = __ldg(p.row_info + jj);
+    }
+  };
+  auto lone_fetch = [&](int32_t s_, int32_t jj, long long &b, double &t, unsigned long long &r) {
+    int idx = jj - lwin_j0;
+    if (lwin_s != s_ || idx < 0 || idx >= 32) {
+      lone_reload(s_, jj);
+      idx = 0;
+    }
+    b = __shfl_sync(0xffffffffu, lwin_b, idx);
+    t = __shfl_sync(0xffffffffu, lwin_t, idx);
+    r = __shfl_sync(0xffffffffu, lwin_r, idx);
   };
 
   for (;;) {
@@ -444,8 +501,57 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       }
     }
     // ---- a warp's last live walk: the idle lanes compute its draws ahead
-    wd.prepare(alive, __any_sync(0xffffffffu, finished), ds, pk.pid, p.key0, p.key1, p.iteration, lane);
+    if (lone) {
+      wd.keep(ds, p.key0, p.key1, p.iteration, lane);
+    } else {
+      wd.prepare(alive, __any_sync(0xffffffffu, finished), ds, pk.pid, p.key0, p.key1, p.iteration, lane);
+      if (wd.on && MODE != 2 && !p.n_virtual) {
+        // enter lone-walker mode: the other lanes' packets are done; they hand
+        // their estimator sums over and take the walk's state
+        owner = __ffs(__ballot_sync(0xffffffffu, alive)) - 1;
+        if (!alive && acc_s >= 0) {
+          atomicAdd(p.j_est + acc_s, acc_j);
+          atomicAdd(p.nu_bar + acc_s, acc_nb);
+        }
+        const unsigned F = 0xffffffffu;
+        pk.p = __shfl_sync(F, pk.p, owner);
+        pk.q = __shfl_sync(F, pk.q, owner);
+        pk.nu_lab = __shfl_sync(F, pk.nu_lab, owner);
+        pk.e_lab = __shfl_sync(F, pk.e_lab, owner);
+        pk.inv_nu = __shfl_sync(F, pk.inv_nu, owner);
+        pk.D = __shfl_sync(F, pk.D, owner);
+        pk.inv_D = __shfl_sync(F, pk.inv_D, owner);
+        pk.nu_cmf = __shfl_sync(F, pk.nu_cmf, owner);
+        pk.eD2 = __shfl_sync(F, pk.eD2, owner);
+        pk.shell = __shfl_sync(F, pk.shell, owner);
+        pk.next_line = __shfl_sync(F, pk.next_line, owner);
+        pk.pid = __shfl_sync(F, pk.pid, owner);
+        pk.have_cmf = __shfl_sync(F, static_cast<int>(pk.have_cmf), owner) != 0;
+#pragma unroll
+        for (int c = 0; c < kNCounters; ++c) pk.cnt[c] = __shfl_sync(F, pk.cnt[c], owner);
+        ds.k0 = __shfl_sync(F, ds.k0, owner);
+        ds.k1 = __shfl_sync(F, ds.k1, owner);
+        ds.packet = __shfl_sync(F, ds.packet, owner);
+        ds.iteration = __shfl_sync(F, ds.iteration, owner);
+        ds.d = __shfl_sync(F, ds.d, owner);
+        ds.spare_a = __shfl_sync(F, ds.spare_a, owner);
+        ds.spare_b = __shfl_sync(F, ds.spare_b, owner);
+        cs = __shfl_sync(F, cs, owner);
+        c_kap = __shfl_sync(F, c_kap, owner);
+        c_ikap = __shfl_sync(F, c_ikap, owner);
+        c_xi2 = __shfl_sync(F, c_xi2, owner);
+        c_xo2 = __shfl_sync(F, c_xo2, owner);
+        acc_s = __shfl_sync(F, acc_s, owner);
+        acc_j = __shfl_sync(F, acc_j, owner);
+        acc_nb = __shfl_sync(F, acc_nb, owner);
+        vdraws = __shfl_sync(F, vdraws, owner);
+        lwin_s = -1;
+        alive = true;
+        lone = true;
+      }
+    }
     if (!alive) continue;
+    const bool act = !lone || static_cast<int>(lane) == owner;  // makes the walk's side effects
 
     // ---- one flight segment (Sect. 2.6)
     int status = 0;
@@ -523,9 +629,14 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       long long bj = 0, bj_n = 0;
       double taul = 0.0, tau_n = 0.0;
       unsigned long long rinfo = 0ull, rinfo_n = 0ull;
-      if (!lw_ok) load_window(s, j);
-      bj = lw_b0; taul = lw_t0; rinfo = lw_r0;
-      bj_n = lw_b1; tau_n = lw_t1; rinfo_n = lw_r1;
+      if (lone) {
+        lone_fetch(s, j, bj, taul, rinfo);
+        lone_fetch(s, j + 1, bj_n, tau_n, rinfo_n);
+      } else {
+        if (!lw_ok) load_window(s, j);
+        bj = lw_b0; taul = lw_t0; rinfo = lw_r0;
+        bj_n = lw_b1; tau_n = lw_t1; rinfo_n = lw_r1;
+      }
       lw_ok = false;
       long long bj_nn = 0;
       double tau_nn = 0.0;
@@ -536,7 +647,9 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         bj_nn = 0;
         tau_nn = 0.0;
         rinfo_nn = 0ull;
-        if (j + 2 < L) {
+        if (lone) {
+          lone_fetch(s, j + 2, bj_nn, tau_nn, rinfo_nn);
+        } else if (j + 2 < L) {
           bj_nn = __ldg(nub + j + 2);
           tau_nn = __ldg(tau_s + j + 2);
           if (MODE >= 1 && p.row_info) rinfo_nn = __ldg(p.row_info + j + 2);
@@ -564,7 +677,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
           have_ev = true;
           if (shell_state == 0 && !inside_shell(pl_ev, r2_ev, inner, xi2, xo2)) break;  // exit comes first
           pk.cnt[2] += 1u;
-          if (JB) atomicAdd(p.j_blue + row + j, e_inv2);
+          if (JB && act) atomicAdd(p.j_blue + row + j, e_inv2);
           kind = kLineEvent;
           l = lj;
           nu_hit = nuj;
@@ -583,7 +696,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
           if (beyond_exit(bj)) break;  // this line lies beyond the exit
         }
         pk.cnt[2] += 1u;
-        if (JB) atomicAdd(p.j_blue + row + j, e_inv2);
+        if (JB && act) atomicAdd(p.j_blue + row + j, e_inv2);
         if (thomson) {
           thr_e = t;
           key_e = rawkey(t);
@@ -629,7 +742,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       // estimators, Eqs. 13-14 (segment-start comoving values)
       const double wgt = eD2 * l;
       if (s != acc_s) {
-        if (acc_s >= 0) {
+        if (acc_s >= 0 && act) {
           atomicAdd(p.j_est + acc_s, acc_j);
           atomicAdd(p.nu_bar + acc_s, acc_nb);
         }
@@ -665,7 +778,8 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
             nu_c = em.nu;
             inv_nu_c = em.inv_nu;
             pk.next_line = em.line + 1;
-            load_window(s, pk.next_line);
+            if (lone) lone_reload(s, pk.next_line);
+            else load_window(s, pk.next_line);
           } else {
             nu_c = nu_hit;
             inv_nu_c = rcp64(nu_hit);
@@ -697,13 +811,20 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         pk.nu_cmf = nu_c;       // = nu_lab D2
         pk.eD2 = e_c * D2;      // = E_lab D2^2
         pk.have_cmf = true;
-        if (p.n_virtual) {
+        if (p.n_virtual && act) {
           spawn_virtual(p, sh, VirtualLaunch{xn, r2n, nu_c, e_c, s, pk.next_line, pk.pid, vdraws, false});
           vdraws += static_cast<uint32_t>(p.n_virtual);
         }
       }
     }
-    if (status != 0) {
+    if (status != 0 && !act) {  // lone mode, not the owner lane: drop the adopted walk
+      alive = false;
+      lone = false;
+      acc_s = -1;
+      acc_j = 0.0;
+      acc_nb = 0.0;
+    } else if (status != 0) {
+      lone = false;
       if (status == 1) ++n_esc;
       else if (status == 2) ++n_reab;
       else ++n_cap;
@@ -725,7 +846,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       alive = false;
     }
   }
-  if (acc_s >= 0) {
+  if (acc_s >= 0 && (!lone || static_cast<int>(lane) == owner)) {  // (a launch stopped in lone mode)
     atomicAdd(p.j_est + acc_s, acc_j);
     atomicAdd(p.nu_bar + acc_s, acc_nb);
   }
