@@ -453,9 +453,10 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
   };
 
   for (;;) {
-    // ---- claim packets for idle lanes (one atomic per warp)
-    const bool need = !alive && !finished;
-    const unsigned needmask = __ballot_sync(0xffffffffu, need);
+    // ---- claim packets for idle lanes (one atomic per warp; none in lone mode,
+    // where every lane carries the walk until it ends)
+    const bool need = !lone && !alive && !finished;
+    const unsigned needmask = lone ? 0u : __ballot_sync(0xffffffffu, need);
     if (needmask) {
       const int leader = __ffs(needmask) - 1;
       unsigned long long base = 0ull;
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         }
       }
     }
-    if (__all_sync(0xffffffffu, finished)) break;
+    if (!lone && __all_sync(0xffffffffu, finished)) break;
     if (p.timeout_ns) {
       bool late = false;
       if (lane == 0u) late = (global_ns() - t_start) > p.timeout_ns;
