@@ -473,7 +473,8 @@ def _log(msg):
     print(f"[bench] {msg}", file=sys.stderr, flush=True)
 
 
-def measure_batched(n_models=256, groups=2, j_blue=True, fp64_models=None, noise_models=16, n_it=10):
+def measure_batched(n_models=256, groups=2, j_blue=True, fp64_models=None, noise_models=16, n_it=10,
+                    order=None):
     """256 uneven models x 10 iterations: batched mixed vs per-model binary64.
 
     The per-model binary64 side runs the first ``fp64_models`` models of the
@@ -523,6 +524,10 @@ def measure_batched(n_models=256, groups=2, j_blue=True, fp64_models=None, noise
         trials += tr_
     tune_s = time.perf_counter() - t0
     _log(f"autotune {tuned} {tuned_ms} ms after {trials} trials ({tune_s:.1f} s)")
+    if order is not None:  # a given queue order with the tuned block size and residency
+        for b, l_ in zip(batches, tuned):
+            b.set_launch(block=l_["block"], blocks_per_sm=l_["blocks_per_sm"], order=order)
+        tuned = [b.launch() for b in batches]
     clocks = ClockSampler(0)
     clocks.start()
     torch.cuda.synchronize()
@@ -639,7 +644,9 @@ def measure_batched(n_models=256, groups=2, j_blue=True, fp64_models=None, noise
 def run_batched(args):
     """256 uneven models x 10 iterations: batched mixed vs per-model binary64."""
     limit = int(os.environ.get("BENCH_FP64_MODELS", str(args.models)))
-    r = measure_batched(args.models, args.groups, bool(args.j_blue), fp64_models=limit)
+    orders = {"auto": None, "packets": 0, "work": 1, "given": 2}
+    r = measure_batched(args.models, args.groups, bool(args.j_blue), fp64_models=limit,
+                        order=orders[args.order])
     value, batched_s = r.pop("value"), r.pop("batched_s")
     line = {
         "metric": "models/s", "value": value, "unit": "models/s", "n_gpus": 1, "steps": 10,
@@ -869,6 +876,8 @@ def main():
     ap.add_argument("--serve-groups", type=int, default=4,
                     help="serving: model groups advancing independently (1 = one tick for all)")
     ap.add_argument("--j-blue", type=int, default=1, choices=[0, 1], help="J_blue estimators (batched workload)")
+    ap.add_argument("--order", default="auto", choices=["auto", "packets", "work", "given"],
+                    help="batched workload: packet queue order (auto = the autotuner's)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
