@@ -93,6 +93,24 @@ __device__ __forceinline__ uint32_t load_sys_u32(const uint32_t *a) {
   return v;
 }
 
+// L2 eviction priority for the J_blue sums: a J_blue array is as large as the
+// Sobolev depths (S x L cells) and is only written, by atomics, during a
+// transport launch; marking those atomics evict-first keeps the line list,
+// the depths and the branching records -- what the random walks read on
+// their dependency chains -- resident in L2 instead.
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void red_add_evict_first(double *a, double v, unsigned long long pol) {
+  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void red_add_evict_first(unsigned long long *a, unsigned long long v,
+                                                    unsigned long long pol) {
+  asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(a), "l"(v), "l"(pol) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

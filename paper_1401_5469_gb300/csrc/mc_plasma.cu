@@ -192,9 +192,11 @@ __global__ void zero_large_kernel(double *a, size_t n) {
   const size_t n2 = n / 2;
   double2 *a2 = reinterpret_cast<double2 *>(a);
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  // streaming stores (evict-first): zeroing the J_blue sums must not push the
+  // line data out of L2
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n2; i += stride)
-    a2[i] = make_double2(0.0, 0.0);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) a[n - 1] = 0.0;
+    __stcs(a2 + i, make_double2(0.0, 0.0));
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) __stcs(a + n - 1, 0.0);
 }
 
 // Per-line constants of Eq. 12 and the level/branching-row indices.
@@ -280,7 +282,7 @@ __global__ void jblue_from_fix_kernel(double *jb, size_t n, double e_cmf, double
   unsigned long long *fix = reinterpret_cast<unsigned long long *>(jb);
   const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n; i += stride)
-    jb[i] = ((static_cast<double>(fix[i]) * (1.0 / kEstFixScale)) * e_cmf) * inv_nu_ref;
+    __stcs(jb + i, ((static_cast<double>(__ldcs(fix + i)) * (1.0 / kEstFixScale)) * e_cmf) * inv_nu_ref);
 }
 
 // Binary64 J_blue: the transport adds E_lab / nu_lab^2 at each Sobolev point
@@ -291,9 +293,9 @@ __global__ void jblue_times_nu_kernel(double *jb, const double *nu, int S, int L
   const int stride = gridDim.x * blockDim.x;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < L; j += stride) {
     const double v = nu[j];
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < S; ++s) {  // streaming loads and stores, as in the zeroing
       double *c = jb + static_cast<size_t>(s) * static_cast<size_t>(L) + j;
-      *c = *c * v;
+      __stcs(c, __ldcs(c) * v);
     }
   }
 }

@@ -372,6 +372,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
 
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lanemask_lt = (1u << lane) - 1u;
+  const unsigned long long jb_pol = l2_evict_first_policy();
   const unsigned long long t_start = global_ns();
   uint32_t polls = 0u;  // loop iterations between looks at the host's stop request
   if (lane == 0u) atomicCAS(p.flags + 3, 0ull, t_start);
@@ -678,7 +679,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
           have_ev = true;
           if (shell_state == 0 && !inside_shell(pl_ev, r2_ev, inner, xi2, xo2)) break;  // exit comes first
           pk.cnt[2] += 1u;
-          if (JB && act) atomicAdd(p.j_blue + row + j, e_inv2);
+          if (JB && act) red_add_evict_first(p.j_blue + row + j, e_inv2, jb_pol);
           kind = kLineEvent;
           l = lj;
           nu_hit = nuj;
@@ -697,7 +698,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
           if (beyond_exit(bj)) break;  // this line lies beyond the exit
         }
         pk.cnt[2] += 1u;
-        if (JB && act) atomicAdd(p.j_blue + row + j, e_inv2);
+        if (JB && act) red_add_evict_first(p.j_blue + row + j, e_inv2, jb_pol);
         if (thomson) {
           thr_e = t;
           key_e = rawkey(t);

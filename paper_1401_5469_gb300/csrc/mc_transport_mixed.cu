@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
   extern __shared__ unsigned long long smem_u64[];
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lanemask_lt = (1u << lane) - 1u;
+  const unsigned long long jb_pol = l2_evict_first_policy();
   MCtx c;
   int32_t cur_model = -1;
   unsigned long long *prefix = smem_u64;
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
             if (bj <= key_shell) break;  // this line lies beyond the exit
           }
           pk.cnt[2] += 1u;
-          if (JB) atomicAdd(c.jb_fix + row + j, __float2ull_rn((f32_of_positive_f64(bj) * inv_nu) * e_jb));
+          if (JB) red_add_evict_first(c.jb_fix + row + j, __float2ull_rn((f32_of_positive_f64(bj) * inv_nu) * e_jb), jb_pol);
           if (thomson) {
             thr_e = t;
             key_e = rawkey(t);
@@ -459,7 +460,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
           const float lj = f32_of_f64_max0(nu_cmf - nuj) * inv_nu;
           if (!have_shell && !inside_shell_f(pp, q, lj, inner, xi2, xo2)) break;  // exit comes first
           pk.cnt[2] += 1u;
-          if (JB) atomicAdd(c.jb_fix + row + j, __float2ull_rn((f32_of_positive_f64(bj) * inv_nu) * e_jb));
+          if (JB) red_add_evict_first(c.jb_fix + row + j, __float2ull_rn((f32_of_positive_f64(bj) * inv_nu) * e_jb), jb_pol);
           kind = kLineEvent;
           l = lj;
           nu_hit = nuj;
