@@ -277,6 +277,15 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
   for (int i = 0; i < kNStats; ++i) st.v[i] = 0ull;
   int32_t acc_s = -1;
   unsigned long long acc_j = 0ull, acc_nb = 0ull;  // fixed point, see kEstFixScale
+  // the lane's current shell and its constants (reloaded on a shell or model change)
+  int32_t cs = -1;
+  float c_kap = 0.0f, c_ikap = 0.0f, c_xi2 = 0.0f, c_xo2 = 0.0f;
+  // single-model build: lines next_line, next_line + 1 of the next segment,
+  // loaded by the event that began it (see the binary64 kernel)
+  bool lw_ok = false;
+  long long lw_b0 = 0, lw_b1 = 0;
+  float lw_t0 = 0.0f, lw_t1 = 0.0f;
+  unsigned long long lw_r0 = 0ull, lw_r1 = 0ull;
 
   for (;;) {
     const bool need = !alive && !finished;
@@ -307,6 +316,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
               acc_s = -1; acc_j = 0ull; acc_nb = 0ull;
               load_ctx(c, p.batch[lo], p.batch[lo].shell32);
               cur_model = lo;
+              cs = -1;
             }
             id -= prefix[lo];
           }
@@ -336,6 +346,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
 #pragma unroll
           for (int k = 0; k < kNCounters; ++k) pk.cnt[k] = 0u;
           alive = true;
+          lw_ok = false;
         } else {
           finished = true;
           atomicCAS(p.flags + 1, 0ull, global_ns());
@@ -376,10 +387,17 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
       const float inv_D = pk.have_inv_D ? pk.inv_D : 1.0f / Df;
       const double nu_cmf = nu_lab * f64_of_f32(Df);
       const float eD2 = (pk.e_lab * Df) * Df;
-      const float kap = c.kap[s];
+      if (s != cs) {
+        cs = s;
+        c_kap = c.kap[s];
+        c_ikap = c.ikap[s];
+        c_xi2 = c.xi2[s];
+        c_xo2 = c.xo2[s];
+      }
+      const float kap = c_kap;
       const bool thomson = kap > 0.0f;
       const float tau0 = -__logf(open0f(ds.next_u53()));
-      const float xi2 = c.xi2[s], xo2 = c.xo2[s];
+      const float xi2 = c_xi2, xo2 = c_xo2;
       const bool inner = pp < 0.0f && q <= xi2;
       // shell exit threshold only once a line is passed or the exit wins
       // (see inside_shell_f)
@@ -390,7 +408,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
       double thr_e = 0.0;
       long long key_e = kKeyNegInf;
       if (thomson) {
-        c_e = (f32_of_positive_f64(__double_as_longlong(nu_lab)) * c.ikap[s]) * inv_D;  // nu_lab / k
+        c_e = (f32_of_positive_f64(__double_as_longlong(nu_lab)) * c_ikap) * inv_D;  // nu_lab / k
         thr_e = nu_cmf - f64_of_f32(tau0 * c_e);
         key_e = rawkey(thr_e);  // compared only with positive keys
       }
@@ -409,21 +427,30 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
       long long bj = 0, bj_n = 0;
       float taul = 0.0f, tau_n = 0.0f;
       unsigned long long rinfo = 0ull, rinfo_n = 0ull;
-      if (j < L) {
-        bj = __ldg(nub + j);
-        taul = __ldg(tau_s + j);
-        if (MODE == 1) rinfo = __ldg(c.row_info + j);
+      if (MINB == 1 && lw_ok) {
+        bj = lw_b0; taul = lw_t0; rinfo = lw_r0;
+        bj_n = lw_b1; tau_n = lw_t1; rinfo_n = lw_r1;
+      } else {
+        if (j < L) {
+          bj = __ldg(nub + j);
+          taul = __ldg(tau_s + j);
+          if (MODE == 1) rinfo = __ldg(c.row_info + j);
+        }
+        if (j + 1 < L) {
+          bj_n = __ldg(nub + j + 1);
+          tau_n = __ldg(tau_s + j + 1);
+          if (MODE == 1) rinfo_n = __ldg(c.row_info + j + 1);
+        }
       }
-      if (j + 1 < L) {
-        bj_n = __ldg(nub + j + 1);
-        tau_n = __ldg(tau_s + j + 1);
-        if (MODE == 1) rinfo_n = __ldg(c.row_info + j + 1);
-      }
+      lw_ok = false;
+      long long bj_nn = 0;
+      float tau_nn = 0.0f;
+      unsigned long long rinfo_nn = 0ull;
       while (j < L) {
         pk.cnt[1] += 1u;
-        long long bj_nn = 0;
-        float tau_nn = 0.0f;
-        unsigned long long rinfo_nn = 0ull;
+        bj_nn = 0;
+        tau_nn = 0.0f;
+        rinfo_nn = 0ull;
         if (j + 2 < L) {
           bj_nn = __ldg(nub + j + 2);
           tau_nn = __ldg(tau_s + j + 2);
@@ -524,15 +551,40 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
             int32_t emit;
             pick_m(c, rinfo_em, ds.next_u53(), nu_c, inv_nu_c, emit);
             pk.next_line = emit + 1;
+            if (MINB == 1) {  // the next segment's first lines, loaded now
+              const int32_t nl = pk.next_line;
+              lw_b0 = 0; lw_t0 = 0.0f; lw_r0 = 0ull; lw_b1 = 0; lw_t1 = 0.0f; lw_r1 = 0ull;
+              if (nl < L) {
+                lw_b0 = __ldg(nub + nl);
+                lw_t0 = __ldg(tau_s + nl);
+                if (MODE == 1) lw_r0 = __ldg(c.row_info + nl);
+              }
+              if (nl + 1 < L) {
+                lw_b1 = __ldg(nub + nl + 1);
+                lw_t1 = __ldg(tau_s + nl + 1);
+                if (MODE == 1) lw_r1 = __ldg(c.row_info + nl + 1);
+              }
+              lw_ok = true;
+            }
           } else {
             nu_c = nu_hit;
             inv_nu_c = 1.0f / f32_of_positive_f64(__double_as_longlong(nu_hit));
             pk.next_line = j + 1;
+            if (MINB == 1) {  // lines j + 1, j + 2 are in the scan's registers
+              lw_b0 = bj_n; lw_t0 = tau_n; lw_r0 = rinfo_n;
+              lw_b1 = bj_nn; lw_t1 = tau_nn; lw_r1 = rinfo_nn;
+              lw_ok = true;
+            }
           }
         } else {
           pk.cnt[4] += 1u;
           nu_c = nu_lab * f64_of_f32(D1);
           inv_nu_c = inv_nu / D1;
+          if (MINB == 1) {  // the next segment starts at line j again
+            lw_b0 = bj; lw_t0 = taul; lw_r0 = rinfo;
+            lw_b1 = bj_n; lw_t1 = tau_n; lw_r1 = rinfo_n;
+            lw_ok = true;
+          }
         }
         const unsigned long long um = ds.next_u53();
         const float mu2 = static_cast<float>(static_cast<long long>(um >> 29) - (1ll << 23)) * 0x1.0p-23f;
