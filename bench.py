@@ -692,7 +692,10 @@ def run_serve(args):
                           n_iterations=int(rng.integers(5, 21)), seed=5469 + k, arrival=a)
             for k, a in enumerate(arrivals)]
     tick_packets = args.tick_packets or (25_000_000 if mixed else 5_000_000)
-    n_groups = max(1, args.serve_groups)
+    # model groups advancing independently: 2 for batched mixed precision (a
+    # group's batch keeps a large packet budget), 8 for binary64 (single-model
+    # launches on 8 streams overlap one another's tails); measured best of 1-16
+    n_groups = args.serve_groups if args.serve_groups > 0 else (2 if mixed else 8)
     server = serve.Server(hbm_budget_bytes=150e9, j_blue=False, precision=prec,
                           max_tick_packets=tick_packets, n_groups=n_groups)
     clocks = ClockSampler(0)
@@ -884,8 +887,9 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--tick-packets", type=int, default=0)
-    ap.add_argument("--serve-groups", type=int, default=4,
-                    help="serving: model groups advancing independently (1 = one tick for all)")
+    ap.add_argument("--serve-groups", type=int, default=0,
+                    help="serving: model groups advancing independently (1 = one tick for all; "
+                         "0 = 2 in mixed precision, 8 in binary64)")
     ap.add_argument("--j-blue", type=int, default=1, choices=[0, 1], help="J_blue estimators (batched workload)")
     ap.add_argument("--order", default="auto", choices=["auto", "packets", "work", "given"],
                     help="batched workload: packet queue order (auto = the autotuner's)")
