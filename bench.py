@@ -69,25 +69,27 @@ L2_BYTES = 129 * 2**20
 # kernel built from these sources only: with any other source hash the
 # bench reports traffic as null.
 TRAFFIC_CAPTURE = {
-    "dram_bytes_per_launch": 625.95e6 + 112.66e6,
+    "dram_bytes_per_launch": 777.38e6 + 131.70e6,
     "sources": ("paper_1401_5469_gb300/csrc/mc_transport.cu", "paper_1401_5469_gb300/csrc/mc_device.cuh",
                 "paper_1401_5469_gb300/csrc/mc_internal.h"),
-    "sha256": "084d987e58e2d50c1bdca8291767a83ddbed811c6efbd79c541c3b08ff2f4445",
+    "sha256": "43e90e509671a99020bd51672412f7f6ed712dce0fcfe7b9265fadcd3309d923",
 }
 
 
-# Binary64 lane operations (DADD + DMUL + DFMA thread instructions) per
-# flight segment of the same kernel, from ncu's sass_thread_inst_executed
-# counters on the 1e5-packet case of this model (profiles/
-# transport_fp64_downbranch_1e5_fp64_ops.md); null for other sources.
+# Binary64 warp instructions (FP64-pipe issue slots) per flight segment of the
+# same kernel, from ncu's sm__inst_executed_pipe_fp64 on one full-size launch
+# of this workload (profiles/transport_fp64_downbranch_500k_fp64_ops.md); null
+# for other sources.  (Lane operations would count the redundant lanes of the
+# lone-walker mode, where the whole warp runs one walk.)
 FP64_OPS_CAPTURE = {
-    "lane_ops_per_segment": 76.71,
+    "warp_instructions_per_segment": 9.356,
     "sources": TRAFFIC_CAPTURE["sources"],
     "sha256": TRAFFIC_CAPTURE["sha256"],
 }
-# Binary64 peak of the FP64 pipes: 2 lane operations per SM per cycle (ncu's
-# peak_sustained for DFMA) x 152 SMs at the 2070 MHz maximum SM clock.
-FP64_PEAK_OPS = 2 * 152 * 2.070e9
+# Binary64 pipe peak in issue slots: one binary64 warp instruction per ~64
+# cycles per SM sub-partition (measured on this GPU with one-warp probes,
+# dependent or not), 4 sub-partitions per SM, 152 SMs, 2070 MHz.
+FP64_PEAK_SLOTS = 4 * 152 * 2.070e9 / 64
 
 
 def _sources_match(capture):
@@ -104,13 +106,15 @@ def _captured_traffic():
 
 
 def _fp64_roofline(segments, seconds):
-    ops = FP64_OPS_CAPTURE["lane_ops_per_segment"]
-    if ops is None or not _sources_match(FP64_OPS_CAPTURE):
+    per = FP64_OPS_CAPTURE["warp_instructions_per_segment"]
+    if per is None or not _sources_match(FP64_OPS_CAPTURE):
         return None
-    achieved = ops * segments / seconds
-    return {"bound": "alu", "achieved": achieved / 1e9, "peak": FP64_PEAK_OPS / 1e9, "unit": "G lane-ops/s",
-            "frac": achieved / FP64_PEAK_OPS, "lane_ops_per_segment": ops, "kernel": "transport_fp64",
-            "peak_kind": "derived: 2 binary64 lanes/SM/cycle x 152 SMs x 2070 MHz"}
+    achieved = per * segments / seconds
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": FP64_PEAK_SLOTS / 1e9,
+            "unit": "G binary64 warp instructions/s", "frac": achieved / FP64_PEAK_SLOTS,
+            "warp_instructions_per_segment": per, "kernel": "transport_fp64",
+            "peak_kind": "derived: 1 binary64 warp instruction per 64 cycles per sub-partition (measured), "
+                         "4 per SM x 152 SMs x 2070 MHz"}
 
 
 def _peaks():
