@@ -11,8 +11,9 @@ updated from the estimators.  The iteration index advances every step.
     python bench.py --workload batched [--models M]
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle (the plain
-FP64 C implementation used by the tests) on a bounded packet sample of the
-same workload.  The default line also carries the mixed-precision loop, the
+FP64 C implementation used by the tests) on all host cores, over the same
+iteration loop (each step the whole 1e6-packet iteration, then the T_R/W
+update; ``BENCH_REF_SAMPLE`` bounds the packets per step).  The default line also carries the mixed-precision loop, the
 2000-line scatter model, and a ``batched`` object: the batched workload below
 (256 models, two groups, mixed precision) with its own roofline, and the
 per-model binary64 path on the first 8 of those models.
