@@ -173,3 +173,43 @@ def test_noalloc_rejects_too_many_shells(env):
         mc.mc_transport_noalloc(args, None)
     assert ei.value.code == mc.MC_ERR_INVALID_ARG
     assert "MC_NOALLOC_MAX_SHELLS" in str(ei.value)
+
+
+_FIRST_CALL_UNDER_CAPTURE = r"""
+import sys
+import torch
+from paper_1401_5469_gb300 import mc
+mc.load()
+args = mc.mc_noalloc_args(n_shells=1, n_lines=1, spec_bins=10)
+dummy = torch.zeros(64, dtype=torch.float64, device="cuda")
+for name in ("v_inner", "v_outer", "n_e", "nu", "tau", "j_est", "nu_bar", "spectrum"):
+    setattr(args, name, dummy.data_ptr())
+args.v_inner_0, args.t_exp, args.t_inner, args.n_packets = 1e9, 1e6, 1e4, 10
+args.spec_nu_lo, args.spec_nu_hi = 1e14, 3e15
+torch.cuda.synchronize()
+g = torch.cuda.CUDAGraph()
+code = None
+try:
+    with torch.cuda.graph(g):
+        try:
+            mc.mc_transport_noalloc(args, torch.cuda.current_stream().cuda_stream)
+        except mc.MCError as e:
+            code = e.code
+            print("refused:", e)
+except Exception as e:  # an empty capture may be reported on exit
+    print("capture end:", type(e).__name__)
+sys.exit(0 if code == mc.MC_ERR_INVALID_ARG else 1)
+"""
+
+
+def test_noalloc_first_call_refused_while_capturing(env):
+    """The first call on a device runs a set-up kernel; made on a capturing
+    stream it would land in a graph that may never run, so it is refused
+    (checked in a fresh process, where the call is the first on the device)."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FIRST_CALL_UNDER_CAPTURE], cwd=root, capture_output=True,
+                       text=True, timeout=300, env={**os.environ, "PYTHONPATH": root})
+    assert r.returncode == 0, (r.stdout[-2000:], r.stderr[-2000:])
+    assert "capturing" in r.stdout
