@@ -197,6 +197,19 @@ __device__ __forceinline__ float f32_rz(double d) {
   return e <= 0 ? 0.0f : __int_as_float((e << 23) | static_cast<int>((b >> 29) & 0x7fffffull));
 }
 
+// binary64 -> binary32 toward zero on the bit pattern, any sign: |result| <=
+// |d| with a relative error below 2^-23, values below the binary32 normal
+// range give (signed) 0, values above its range (and NaN) +-infinity.
+__device__ __forceinline__ float f32_rz_any(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const int e = static_cast<int>((b >> 52) & 0x7ffull) - 1023 + 127;
+  const unsigned int mag = e <= 0 ? 0u
+                           : e >= 255 ? 0x7f800000u
+                                      : (static_cast<unsigned int>(e) << 23) |
+                                            static_cast<unsigned int>((b >> 29) & 0x7fffffull);
+  return __int_as_float(static_cast<int>(mag | (static_cast<unsigned int>(b >> 63) << 31)));
+}
+
 // Bit pattern of the binary64 value of a positive normal binary32 (exact).
 __device__ __forceinline__ long long f64_bits(float f) {
   const unsigned int b = static_cast<unsigned int>(__float_as_int(f));
@@ -626,14 +639,109 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       double l = 0.0, nu_hit = 0.0;
       double pl_ev = 0.0, r2_ev = 0.0;  // x mu and x^2 at the event, when the exit test made them
       bool have_ev = false;
+      double D1_ev = 0.0;  // Doppler factor at the event point, when the scan made it
       unsigned long long rinfo_hit = 0ull;
       // two lines ahead are always in flight while line j is resolved
       long long bj = 0, bj_n = 0;
       double taul = 0.0, tau_n = 0.0;
       unsigned long long rinfo = 0ull, rinfo_n = 0ull;
+      // An absorbing line (Sect. 2.6): the Sobolev point nu_lab (1 - x mu) =
+      // nu_j, so x mu = 1 - nu_j / nu_lab and D = nu_j / nu_lab there (a
+      // resonance that rounding puts behind the packet is taken where the
+      // packet is).  With no line passed yet the event point is also placed
+      // against the shell exit; if the exit comes first the scan ends with no
+      // event (kind stays 0).
+      auto absorb = [&](long long b_, unsigned long long r_) {
+        const double nuj = __longlong_as_double(b_);
+        const double lj = max0(fma(-nuj, inv_nu, D));
+        const bool ahead = rawkey(lj) > 0;
+        pl_ev = ahead ? fma(-nuj, inv_nu, 1.0) : pp;
+        D1_ev = ahead ? nuj * inv_nu : D;
+        r2_ev = fma(pl_ev, pl_ev, q);
+        have_ev = true;
+        if (shell_state == 0 && !inside_shell(pl_ev, r2_ev, inner, xi2, xo2)) return;  // exit comes first
+        pk.cnt[2] += 1u;
+        if (JB && act) red_add_evict_first(p.j_blue + row + j, e_inv2, jb_pol);
+        kind = kLineEvent;
+        l = lj;
+        nu_hit = nuj;
+        rinfo_hit = r_;
+      };
+      bool fast = false;  // the lone scan below settled the segment's line event
       if (lone) {
-        lone_fetch(s, j, bj, taul, rinfo);
-        lone_fetch(s, j + 1, bj_n, tau_n, rinfo_n);
+        int idx = j - lwin_j0;
+        if (lwin_s != s || idx < 0 || idx >= 32) {
+          lone_reload(s, j);
+          idx = 0;
+        }
+        if (thomson) {
+          // The scan of lines j0 + idx .. j0 + 31 of the window in one step, lane
+          // k taking line j0 + k.  In exact arithmetic the scan below stops at
+          // line k when nu_k <= T_{k-1} (beyond d_e), when nu_k lies beyond the
+          // shell exit, or when T_k > nu_k (absorbed), with T_k = thr_e + c_e
+          // (tau_idx + ... + tau_k).  Each lane forms A = nu_k - T_{k-1} and B =
+          // nu_k - T_k in binary32 from the exact binary64 difference nu_k - thr_e
+          // (one binary64 instruction for the whole window) and a prefix sum of
+          // the depths, with a bound M on |error| that also covers the rounding
+          // of the scan's own chain of fmas (at most 32 of them).  Where every
+          // sign up to the first line that stops the scan is certain and that
+          // line absorbs, the result is the scan's; otherwise (a sign within
+          // the bound, the exit, d_e or the end of the window reached) the scan
+          // below runs as usual.  Error budget (u = 2^-24): the difference
+          // truncated to binary32 (2u), the depths truncated (2u) and summed in
+          // five levels (5u), c_e truncated (2u), the product and the final
+          // difference (u each), so |A|, |B| error <= 3u |d| + 11u C; the fma
+          // chain adds at most 2^-48 (|thr_e| + C); depths below the binary32
+          // normal range add at most 32 c_e 2^-126.  M = 2^-20 (|d| + C) +
+          // 2^-44 |thr_e| + c_e 2^-119 + 2^-124 bounds all of it.
+          const ShellBracket sb = shell_bracket(q, inner ? xi2 : xo2, inner, nu_lab);
+          const int32_t jl = lwin_j0 + static_cast<int32_t>(lane);
+          const bool cand = static_cast<int>(lane) >= idx;
+          const bool valid = cand && jl < L;
+          const float dk = f32_rz_any(__longlong_as_double(lwin_b) - thr_e);
+          float P = valid ? f32_rz_any(lwin_t) : 0.0f;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(0xffffffffu, P, o);
+            if (static_cast<int>(lane) >= o) P = __fadd_rn(P, y);
+          }
+          float Px = __shfl_up_sync(0xffffffffu, P, 1);
+          if (lane == 0u) Px = 0.0f;
+          const float ce = f32_rz_any(c_e);
+          const float C = __fmul_rn(ce, P);
+          const float A = __fsub_rn(dk, __fmul_rn(ce, Px)), B = __fsub_rn(dk, C);
+          const float M = __fadd_rn(__fmul_rn(0x1.0p-20f, __fadd_rn(fabsf(dk), C)),
+                                    __fadd_rn(__fmul_rn(0x1.0p-44f, fabsf(f32_rz_any(thr_e))),
+                                              __fmaf_rn(ce, 0x1.0p-119f, 0x1.0p-124f)));
+          const bool e_no = A > M;                               // certainly before d_e
+          const bool a_yes = B < -M, a_no = B > M;               // certainly absorbed / passed
+          const bool x_no = sb.ok && lwin_b > sb.hi;             // certainly before the exit
+          const bool pass = valid && e_no && a_no && x_no;
+          const bool take = valid && e_no && a_yes && (static_cast<int>(lane) == idx || x_no);
+          const unsigned stop = __ballot_sync(0xffffffffu, cand && !pass);
+          const unsigned took = __ballot_sync(0xffffffffu, take);
+          const int kstar = __ffs(stop) - 1;
+          if (kstar >= 0 && ((took >> kstar) & 1u)) {
+            fast = true;
+            const int npass = kstar - idx;
+            pk.cnt[1] += static_cast<uint32_t>(npass + 1);
+            pk.cnt[2] += static_cast<uint32_t>(npass);
+            if (JB && cand && static_cast<int>(lane) < kstar)  // the lines passed, one lane each
+              red_add_evict_first(p.j_blue + row + jl, e_inv2, jb_pol);
+            if (npass > 0) {  // as the scan leaves it after its first pass
+              klo = sb.lo;
+              khi = sb.hi;
+              shell_state = 1;
+            }
+            j = lwin_j0 + kstar;
+            bj = __shfl_sync(0xffffffffu, lwin_b, kstar);
+            rinfo = __shfl_sync(0xffffffffu, lwin_r, kstar);
+          }
+        }
+        if (!fast) {
+          lone_fetch(s, j, bj, taul, rinfo);
+          lone_fetch(s, j + 1, bj_n, tau_n, rinfo_n);
+        }
       } else {
         if (!lw_ok) load_window(s, j);
         bj = lw_b0; taul = lw_t0; rinfo = lw_r0;
@@ -643,8 +751,8 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       long long bj_nn = 0;
       double tau_nn = 0.0;
       unsigned long long rinfo_nn = 0ull;
-      double D1_ev = 0.0;  // Doppler factor at the event point, when the scan made it
-      while (j < L) {
+      if (fast) absorb(bj, rinfo);
+      else while (j < L) {
         pk.cnt[1] += 1u;
         bj_nn = 0;
         tau_nn = 0.0;
@@ -658,7 +766,6 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         }
         if (bj <= key_e) break;                             // the Sobolev point lies beyond d_e
         if (shell_state != 0 && beyond_exit(bj)) break;     // ... or beyond the shell exit
-        const double nuj = __longlong_as_double(bj);
         bool absorbed;
         double t = 0.0;
         if (thomson) {
@@ -668,22 +775,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
           absorbed = rawkey(taul) > rawkey(tau_rem);  // both >= 0
         }
         if (absorbed) {
-          const double lj = max0(fma(-nuj, inv_nu, D));
-          // the Sobolev point: nu_lab (1 - x mu) = nu_j, so x mu = 1 - nu_j / nu_lab
-          // and D = nu_j / nu_lab there (a resonance that rounding puts behind
-          // the packet is taken where the packet is)
-          const bool ahead = rawkey(lj) > 0;
-          pl_ev = ahead ? fma(-nuj, inv_nu, 1.0) : pp;
-          D1_ev = ahead ? nuj * inv_nu : D;
-          r2_ev = fma(pl_ev, pl_ev, q);
-          have_ev = true;
-          if (shell_state == 0 && !inside_shell(pl_ev, r2_ev, inner, xi2, xo2)) break;  // exit comes first
-          pk.cnt[2] += 1u;
-          if (JB && act) red_add_evict_first(p.j_blue + row + j, e_inv2, jb_pol);
-          kind = kLineEvent;
-          l = lj;
-          nu_hit = nuj;
-          rinfo_hit = rinfo;
+          absorb(bj, rinfo);
           break;
         }
         if (shell_state == 0) {  // a line is passed: the scan needs the exit frequency
