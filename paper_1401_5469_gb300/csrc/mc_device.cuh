@@ -309,6 +309,9 @@ struct WarpDraws {
     if (!UNBOUNDED || i < kWarpDraws) return u[i];
     return u53_past_buffer(ds.k0, ds.k1, ds.packet, ds.iteration, ds.d - 1u);
   }
+  // The draw next_u53 returns next, without taking it; only while the buffer
+  // holds it (lone-walker mode, within a segment's three draws).
+  __device__ __forceinline__ unsigned long long peek_u53(const DrawStream &ds) const { return u[ds.d - base]; }
   template <bool UNBOUNDED>
   __device__ __forceinline__ double next_tau(DrawStream &ds) const {
     if (!on) return neg_log_u53(ds.next_u53() + 1ull);

@@ -668,6 +668,10 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         rinfo_hit = r_;
       };
       bool fast = false;  // the lone scan below settled the segment's line event
+      // downbranch: the absorbing line's emission record, loaded as soon as the
+      // lone scan names the line (the emission draw is the next in the buffer)
+      bool have_slot = false;
+      ulonglong2 slot_a = make_ulonglong2(0ull, 0ull), slot_c = make_ulonglong2(0ull, 0ull);
       if (lone) {
         int idx = j - lwin_j0;
         if (lwin_s != s || idx < 0 || idx >= 32) {
@@ -736,6 +740,10 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
             j = lwin_j0 + kstar;
             bj = __shfl_sync(0xffffffffu, lwin_b, kstar);
             rinfo = __shfl_sync(0xffffffffu, lwin_r, kstar);
+            if (MODE == 1 && p.dbr_rec) {
+              load_slot(bucket_slot(p, rinfo, wd.peek_u53(ds)), slot_a, slot_c);
+              have_slot = true;
+            }
           }
         }
         if (!fast) {
@@ -868,7 +876,9 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
             // MODE 2: macro atom, internal jumps before the emission pick
             const unsigned long long rinfo_em =
                 MODE == 2 ? macroatom_walk(p, __ldg(p.line_row + j), wd, ds) : rinfo_hit;
-            const Emission em = downbranch_pick(p, j, rinfo_em, wd.template next_u53<MODE == 2>(ds));
+            const unsigned long long u_em = wd.template next_u53<MODE == 2>(ds);
+            const Emission em = have_slot ? pick_from_slot(p, rinfo_em, u_em, slot_a, slot_c)
+                                          : downbranch_pick(p, j, rinfo_em, u_em);
             nu_c = em.nu;
             inv_nu_c = em.inv_nu;
             pk.next_line = em.line + 1;
