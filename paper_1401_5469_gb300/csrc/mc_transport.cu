@@ -42,7 +42,11 @@ constexpr int kLineEvent = 1, kElectronEvent = 2, kShellEvent = 3;
 
 struct Packet {
   double p, q;               // x mu, x^2 - p^2
-  double nu_lab, e_lab, inv_nu;
+  // nu_lab, 1/nu_lab and E_lab / nu_lab = E_cmf / nu_cmf: the first-order
+  // Doppler factor scales energy and frequency alike, so the ratio is the
+  // same in both frames; it changes only when a line re-emits at another
+  // frequency (Thomson and resonant scatterings keep both comoving values).
+  double nu_lab, e_per_nu, inv_nu;
   // Frame quantities at the start of the next flight segment, carried from
   // the event that began it (valid while have_cmf): D = 1 - p, 1/D, the
   // comoving frequency nu_lab D and E_cmf D = E_lab D^2 (the estimators'
@@ -270,9 +274,10 @@ __device__ __forceinline__ double inject(const TransportParams &p, const double 
   const double iD = rcp64(D);
   pk.p = pp;
   pk.q = max0(fma(-pp, pp, x0sq));
+  const double inv_nu_cmf = rcp64(nu_cmf);
   pk.nu_lab = nu_cmf * iD;
-  pk.e_lab = p.e_cmf * iD;
-  pk.inv_nu = rcp64(nu_cmf) * D;
+  pk.e_per_nu = p.e_cmf * inv_nu_cmf;
+  pk.inv_nu = inv_nu_cmf * D;
   pk.D = D;
   pk.inv_D = iD;
   pk.nu_cmf = nu_cmf;
@@ -532,7 +537,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         pk.p = __shfl_sync(F, pk.p, owner);
         pk.q = __shfl_sync(F, pk.q, owner);
         pk.nu_lab = __shfl_sync(F, pk.nu_lab, owner);
-        pk.e_lab = __shfl_sync(F, pk.e_lab, owner);
+        pk.e_per_nu = __shfl_sync(F, pk.e_per_nu, owner);
         pk.inv_nu = __shfl_sync(F, pk.inv_nu, owner);
         pk.D = __shfl_sync(F, pk.D, owner);
         pk.inv_D = __shfl_sync(F, pk.inv_D, owner);
@@ -583,7 +588,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         pk.D = D0;
         pk.inv_D = rcp64(D0);
         pk.nu_cmf = nu_lab * D0;
-        pk.eD2 = (pk.e_lab * D0) * D0;
+        pk.eD2 = (pk.e_per_nu * pk.nu_cmf) * D0;  // E_cmf D
         pk.have_cmf = true;
       }
       const double D = pk.D, inv_D = pk.inv_D, nu_cmf = pk.nu_cmf, eD2 = pk.eD2;
@@ -631,7 +636,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       }
       // J_blue weight of this segment, E_lab / nu_lab^2 (Eq. 17 without its
       // line factor nu_j, applied per cell after the launch)
-      const double e_inv2 = JB ? (pk.e_lab * inv_nu) * inv_nu : 0.0;
+      const double e_inv2 = JB ? pk.e_per_nu * inv_nu : 0.0;
       const size_t row = static_cast<size_t>(s) * static_cast<size_t>(L);
       const double *tau_s = p.tau + row;
       int32_t j = pk.next_line;
@@ -639,7 +644,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       double l = 0.0, nu_hit = 0.0;
       double pl_ev = 0.0, r2_ev = 0.0;  // x mu and x^2 at the event, when the exit test made them
       bool have_ev = false;
-      double D1_ev = 0.0;  // Doppler factor at the event point, when the scan made it
+      double D1_ev = 0.0;  // Doppler factor at an electron-scattering point
       unsigned long long rinfo_hit = 0ull;
       // two lines ahead are always in flight while line j is resolved
       long long bj = 0, bj_n = 0;
@@ -656,7 +661,6 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         const double lj = max0(fma(-nuj, inv_nu, D));
         const bool ahead = rawkey(lj) > 0;
         pl_ev = ahead ? fma(-nuj, inv_nu, 1.0) : pp;
-        D1_ev = ahead ? nuj * inv_nu : D;
         r2_ev = fma(pl_ev, pl_ev, q);
         have_ev = true;
         if (shell_state == 0 && !inside_shell(pl_ev, r2_ev, inner, xi2, xo2)) return;  // exit comes first
@@ -867,11 +871,12 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         // move to the event point (x mu, x^2 and D there from the scan)
         const double r2n = r2_ev;
         const double xn = sqrt64(r2n);
-        const double D1 = D1_ev;
-        const double e_c = pk.e_lab * D1;
-        double nu_c, inv_nu_c;
+        // comoving energy at the event: E / nu times the comoving frequency
+        // there (the line's own frequency at a Sobolev point)
+        double nu_c, inv_nu_c, e_c;
         if (kind == kLineEvent) {
           pk.cnt[3] += 1u;
+          e_c = pk.e_per_nu * nu_hit;
           if (MODE >= 1) {
             // MODE 2: macro atom, internal jumps before the emission pick
             const unsigned long long rinfo_em =
@@ -881,6 +886,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
                                           : downbranch_pick(p, j, rinfo_em, u_em);
             nu_c = em.nu;
             inv_nu_c = em.inv_nu;
+            pk.e_per_nu = e_c * inv_nu_c;  // re-emitted at another frequency
             pk.next_line = em.line + 1;
             if (lone) lone_reload(s, pk.next_line);
             else load_window(s, pk.next_line);
@@ -894,8 +900,9 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
           }
         } else {
           pk.cnt[4] += 1u;
-          nu_c = nu_lab * D1;
-          inv_nu_c = inv_nu * rcp64(D1);
+          nu_c = nu_lab * D1_ev;
+          inv_nu_c = inv_nu * rcp64(D1_ev);
+          e_c = pk.e_per_nu * nu_c;
           lw_ok = true;  // the next segment starts at line j again
           lw_b0 = bj; lw_t0 = taul; lw_r0 = rinfo;
           lw_b1 = bj_n; lw_t1 = tau_n; lw_r1 = rinfo_n;
@@ -908,7 +915,6 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
         pk.p = pn;
         pk.q = max0(fma(-pn, pn, r2n));
         pk.nu_lab = nu_c * iD2;
-        pk.e_lab = e_c * iD2;
         pk.inv_nu = inv_nu_c * D2;
         pk.D = D2;
         pk.inv_D = iD2;
@@ -938,11 +944,12 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       n_lint += pk.cnt[3];
       n_esca += pk.cnt[4];
       n_shell += pk.cnt[5];
-      if (status == 1) atomicAdd(p.spectrum + spectrum_bin(p, pk.nu_lab), pk.e_lab);
+      const double e_lab = pk.e_per_nu * pk.nu_lab;
+      if (status == 1) atomicAdd(p.spectrum + spectrum_bin(p, pk.nu_lab), e_lab);
       if (REC) {
         p.rec_status[pk.pid - p.first_packet] = status;
         p.rec_nu[pk.pid - p.first_packet] = pk.nu_lab;
-        p.rec_e[pk.pid - p.first_packet] = pk.e_lab;
+        p.rec_e[pk.pid - p.first_packet] = e_lab;
 #pragma unroll
         for (int c = 0; c < kNCounters; ++c)
           p.rec_cnt[static_cast<size_t>(pk.pid - p.first_packet) * kNCounters + c] = pk.cnt[c];
