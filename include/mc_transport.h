@@ -527,6 +527,10 @@ mc_status mc_transport_noalloc(const mc_noalloc_args *args, void *stream);
  *   fn = MC_MATH_RCP:  in = double x[n] (normal); ours = reciprocal, ref = 1.0 / x
  *   fn = MC_MATH_SQRT: in = double x[n] >= 0 (0 or normal); ours = square root,
  *        ref = sqrt(x) (IEEE, correctly rounded)
+ *   fn = MC_MATH_APPROX: in = double x[n] > 0 (normal); ours = 1 - x y^2 with
+ *        y = rsqrt.approx.ftz.f64(x), ref = 1 - x r with r = rcp.approx.ftz.f64(x)
+ *        (each by one fma after the product x y): the residuals that the
+ *        square root's and the reciprocal's corrections assume small
  *
  * `in`, `ours` and `ref` are HOST arrays of n elements (0 < n <= 2^28); the
  * call allocates device memory, runs synchronously and frees it (a test
@@ -537,6 +541,7 @@ mc_status mc_transport_noalloc(const mc_noalloc_args *args, void *stream);
 #define MC_MATH_LOG 1
 #define MC_MATH_RCP 2
 #define MC_MATH_SQRT 3
+#define MC_MATH_APPROX 4
 mc_status mc_selftest_math(int32_t fn, const void *in, uint64_t n, double *ours, double *ref);
 
 /* Static description of a status code. */

@@ -1,7 +1,8 @@
 // mc_selftest_math: evaluates the device arithmetic that the transport
 // kernels use in place of CUDA's functions (the table-driven logarithms and
 // the Newton reciprocal and square root of mc_device.cuh) side by side with
-// CUDA's own log, IEEE division and IEEE square root, on inputs the caller
+// CUDA's own log, IEEE division and IEEE square root, and the residuals of
+// the hardware approximations those start from, on inputs the caller
 // chooses.  A diagnostic for accuracy tests; not on the transport path.
 #include <cstdint>
 #include <string>
@@ -36,10 +37,19 @@ __global__ void selftest_kernel(int fn, const unsigned long long *u, const doubl
       ours[i] = rcp64(x[i]);
       ref[i] = 1.0 / x[i];
       break;
-    default:
+    case MC_MATH_SQRT:
       ours[i] = sqrt64(x[i]);
       ref[i] = sqrt(x[i]);
       break;
+    default: {  // MC_MATH_APPROX
+      const double v = x[i];
+      double y, r;
+      asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(v));
+      asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(v));
+      ours[i] = fma(-(v * y), y, 1.0);
+      ref[i] = fma(-v, r, 1.0);
+      break;
+    }
   }
 }
 
@@ -51,7 +61,7 @@ mc_status fail(const std::string &msg) {
 }  // namespace
 
 extern "C" mc_status mc_selftest_math(int32_t fn, const void *in, uint64_t n, double *ours, double *ref) {
-  if (fn < MC_MATH_NEG_LOG_U53 || fn > MC_MATH_SQRT) {
+  if (fn < MC_MATH_NEG_LOG_U53 || fn > MC_MATH_APPROX) {
     set_create_error("mc_selftest_math: unknown function code");
     return MC_ERR_INVALID_ARG;
   }

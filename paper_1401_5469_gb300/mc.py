@@ -50,7 +50,7 @@ EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_run_iter
             "mc_selftest_math")
 
 MC_ORDER_PACKETS, MC_ORDER_WORK, MC_ORDER_GIVEN = 0, 1, 2
-MC_MATH_NEG_LOG_U53, MC_MATH_LOG, MC_MATH_RCP, MC_MATH_SQRT = 0, 1, 2, 3
+MC_MATH_NEG_LOG_U53, MC_MATH_LOG, MC_MATH_RCP, MC_MATH_SQRT, MC_MATH_APPROX = 0, 1, 2, 3, 4
 
 
 class mc_geometry_desc(C.Structure):

@@ -10,6 +10,12 @@ transport kernels, evaluated on the GPU through mc_selftest_math.
     frequencies (Sect. 2.5 frame transforms): within 1 ulp of IEEE division.
   * Square roots of the move and shell-exit geometry (Sect. 2.6): within
     1 ulp of IEEE sqrt; sqrt(0) = 0.
+  * The hardware approximations the reciprocal and square root start from:
+    over every high word of [1, 4) (both exponent parities, four low words
+    each) the residual |1 - x y^2| of rsqrt.approx.f64 stays below 2^-18.5,
+    so the square root's omitted 5e^3/16 term is below 2^-56 relative, and
+    |1 - x r| of rcp.approx.f64 below 2^-19.5, so the reciprocal's omitted
+    e^3 term is below 2^-58.
 """
 import numpy as np
 import pytest
@@ -104,3 +110,16 @@ def test_sqrt64(mc):
     assert ours[0] == 0.0
     nz = ref != 0
     assert _ulps(ours[nz], ref[nz]).max() <= 1.0
+
+
+def test_approximation_residuals(mc):
+    hi = np.arange(1 << 21, dtype=np.uint64)
+    expo = (1023 + (hi >> np.uint64(20))) << np.uint64(52)
+    mant = (hi & np.uint64(0xFFFFF)) << np.uint64(32)
+    lows = np.array([0, 0x80000000, 0xFFFFFFFF, 0x12345678], dtype=np.uint64)
+    bits = (expo[:, None] | mant[:, None] | lows[None, :]).ravel()
+    x = bits.view(np.float64)
+    assert x.min() >= 1.0 and x.max() < 4.0
+    res_rsqrt, res_rcp = mc.mc_selftest_math(mc.MC_MATH_APPROX, x)
+    assert np.abs(res_rsqrt).max() <= 2.0 ** -18.5, np.log2(np.abs(res_rsqrt).max())
+    assert np.abs(res_rcp).max() <= 2.0 ** -19.5, np.log2(np.abs(res_rcp).max())
