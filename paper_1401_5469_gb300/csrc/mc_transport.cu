@@ -117,6 +117,39 @@ __device__ __forceinline__ Emission pick_from_slot(const TransportParams &p, uns
   return em;
 }
 
+// Lone-walker mode (all 32 lanes converged on one walk): the pick from the
+// bucket slot's record, and past it the next 32 records of the row in one
+// coalesced load per round (lane i takes entry i), the first with u below
+// its threshold found by a vote.  The row's last threshold is 2^53 > u, so
+// the search ends inside the row.
+__device__ __forceinline__ Emission pick_from_slot_lone(const TransportParams &p, unsigned long long rinfo,
+                                                        unsigned long long u, ulonglong2 a, ulonglong2 c,
+                                                        unsigned lane) {
+  Emission em;
+  if (u < a.x) {
+    em.nu = __longlong_as_double(static_cast<long long>(a.y));
+    em.inv_nu = __longlong_as_double(static_cast<long long>(c.x));
+    em.line = static_cast<int32_t>(static_cast<uint32_t>(c.y));
+    return em;
+  }
+  const uint32_t end = static_cast<uint32_t>(rinfo) + static_cast<uint32_t>(rinfo >> 32);
+  uint32_t i0 = static_cast<uint32_t>(rinfo) + static_cast<uint32_t>(c.y >> 32) + 1u;
+  for (;;) {
+    const uint32_t i = i0 + lane;
+    ulonglong2 ra = make_ulonglong2(~0ull, 0ull), rc = make_ulonglong2(0ull, 0ull);
+    if (i < end) load_slot(p.dbr_rec + i, ra, rc);
+    const unsigned m = __ballot_sync(0xffffffffu, u < ra.x);  // lanes past the row's end vote yes
+    if (m != 0u) {
+      const int k = __ffs(m) - 1;
+      em.nu = __longlong_as_double(__shfl_sync(0xffffffffu, static_cast<long long>(ra.y), k));
+      em.inv_nu = __longlong_as_double(__shfl_sync(0xffffffffu, static_cast<long long>(rc.x), k));
+      em.line = __shfl_sync(0xffffffffu, static_cast<int32_t>(static_cast<uint32_t>(rc.y)), k);
+      return em;
+    }
+    i0 += 32u;
+  }
+}
+
 __device__ __forceinline__ Emission downbranch_pick(const TransportParams &p, int32_t j,
                                                     unsigned long long rinfo, unsigned long long u) {
   Emission em;
@@ -882,7 +915,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
             const unsigned long long rinfo_em =
                 MODE == 2 ? macroatom_walk(p, __ldg(p.line_row + j), wd, ds) : rinfo_hit;
             const unsigned long long u_em = wd.template next_u53<MODE == 2>(ds);
-            const Emission em = have_slot ? pick_from_slot(p, rinfo_em, u_em, slot_a, slot_c)
+            const Emission em = have_slot ? pick_from_slot_lone(p, rinfo_em, u_em, slot_a, slot_c, lane)
                                           : downbranch_pick(p, j, rinfo_em, u_em);
             nu_c = em.nu;
             inv_nu_c = em.inv_nu;
