@@ -79,6 +79,19 @@ constexpr long long kKeyNegInf = (long long)0xfff0000000000000ll;
 // A pattern below that of every non-negative value.
 constexpr long long kRawBelowZero = (long long)0x8000000000000000ll;
 
+// binary64 -> binary32 toward zero on the bit pattern, any sign: |result| <=
+// |d| with a relative error below 2^-23, values below the binary32 normal
+// range give (signed) 0, values above its range (and NaN) +-infinity.
+__device__ __forceinline__ float f32_rz_any(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const int e = static_cast<int>((b >> 52) & 0x7ffull) - 1023 + 127;
+  const unsigned int mag = e <= 0 ? 0u
+                           : e >= 255 ? 0x7f800000u
+                                      : (static_cast<unsigned int>(e) << 23) |
+                                            static_cast<unsigned int>((b >> 29) & 0x7fffffull);
+  return __int_as_float(static_cast<int>(mag | (static_cast<unsigned int>(b >> 63) << 31)));
+}
+
 // v < 0, excluding -0 (its pattern is the most negative integer).
 __device__ __forceinline__ bool strictly_negative(double v) {
   const long long b = __double_as_longlong(v);
@@ -298,6 +311,23 @@ struct WarpDraws {
     base = b;
     pid = ds.packet;
   }
+  // As keep(), for a kernel that takes only the u53 values from the buffer
+  // (the mixed-precision kernel's log is binary32): the -ln z half stays unset.
+  __device__ __forceinline__ void keep_u(const DrawStream &ds, uint32_t k0, uint32_t k1, uint32_t iteration,
+                                         unsigned lane) {
+    if (ds.packet == pid && ds.d + 3u <= base + kWarpDraws) return;
+    const uint32_t b = ds.d & ~1u;
+    const uint4 o = philox4x32_10(make_uint4((b >> 1) + lane, ds.packet, iteration, 0u), k0, k1);
+    __syncwarp();  // every lane has read the old contents
+    u[2 * lane] = DrawStream::u53_of(o.x, o.y);
+    u[2 * lane + 1] = DrawStream::u53_of(o.z, o.w);
+    __syncwarp();
+    base = b;
+    pid = ds.packet;
+  }
+  // The lone walker's next draw, from the buffer that keep() or keep_u()
+  // holds filled for the segment.
+  __device__ __forceinline__ unsigned long long take_u53(DrawStream &ds) const { return u[ds.d++ - base]; }
   // The live lane's next draw (u53, or the -ln z of an open-interval draw).
   // UNBOUNDED: a segment may take more draws than the buffer holds (a macro
   // atom's internal jumps), and past its end a draw is computed on its own;

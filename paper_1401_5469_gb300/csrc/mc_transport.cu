@@ -234,19 +234,6 @@ __device__ __forceinline__ float f32_rz(double d) {
   return e <= 0 ? 0.0f : __int_as_float((e << 23) | static_cast<int>((b >> 29) & 0x7fffffull));
 }
 
-// binary64 -> binary32 toward zero on the bit pattern, any sign: |result| <=
-// |d| with a relative error below 2^-23, values below the binary32 normal
-// range give (signed) 0, values above its range (and NaN) +-infinity.
-__device__ __forceinline__ float f32_rz_any(double d) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
-  const int e = static_cast<int>((b >> 52) & 0x7ffull) - 1023 + 127;
-  const unsigned int mag = e <= 0 ? 0u
-                           : e >= 255 ? 0x7f800000u
-                                      : (static_cast<unsigned int>(e) << 23) |
-                                            static_cast<unsigned int>((b >> 29) & 0x7fffffull);
-  return __int_as_float(static_cast<int>(mag | (static_cast<unsigned int>(b >> 63) << 31)));
-}
-
 // Bit pattern of the binary64 value of a positive normal binary32 (exact).
 __device__ __forceinline__ long long f64_bits(float f) {
   const unsigned int b = static_cast<unsigned int>(__float_as_int(f));

@@ -179,6 +179,41 @@ __device__ __forceinline__ void pick_m(const MCtx &c, unsigned long long rinfo, 
 
 __device__ __forceinline__ float max0f(float v) { return v > 0.0f ? v : 0.0f; }
 
+// Lone-walker mode (all 32 lanes of the warp converged on one walk): the
+// emission from a bucket slot loaded ahead as two 16-byte halves {thr, nu},
+// {inv_nu, emit | guide << 32}; past the slot the next 32 records of the row
+// in one coalesced load per round (lane i takes entry i), the first with u
+// below its threshold found by a vote (the row's last threshold is 2^53 > u).
+__device__ __forceinline__ void pick_lone_m(const MCtx &c, unsigned long long rinfo, unsigned long long u,
+                                            ulonglong2 a, ulonglong2 h, unsigned lane, double &nu,
+                                            float &inv_nu, int32_t &line) {
+  if (u < a.x) {
+    nu = __longlong_as_double(static_cast<long long>(a.y));
+    inv_nu = f32_of_positive_f64(static_cast<long long>(h.x));
+    line = static_cast<int32_t>(static_cast<uint32_t>(h.y));
+    return;
+  }
+  const uint32_t end = static_cast<uint32_t>(rinfo) + static_cast<uint32_t>(rinfo >> 32);
+  uint32_t i0 = static_cast<uint32_t>(rinfo) + static_cast<uint32_t>(h.y >> 32) + 1u;
+  for (;;) {
+    const uint32_t i = i0 + lane;
+    ulonglong2 ra = make_ulonglong2(~0ull, 0ull), rh = make_ulonglong2(0ull, 0ull);
+    if (i < end) {
+      ra = __ldg(reinterpret_cast<const ulonglong2 *>(c.rec + i));
+      rh = __ldg(reinterpret_cast<const ulonglong2 *>(c.rec + i) + 1);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, u < ra.x);  // lanes past the row's end vote yes
+    if (m != 0u) {
+      const int k = __ffs(m) - 1;
+      nu = __longlong_as_double(__shfl_sync(0xffffffffu, static_cast<long long>(ra.y), k));
+      inv_nu = f32_of_positive_f64(__shfl_sync(0xffffffffu, static_cast<long long>(rh.x), k));
+      line = __shfl_sync(0xffffffffu, static_cast<int32_t>(static_cast<uint32_t>(rh.y)), k);
+      return;
+    }
+    i0 += 32u;
+  }
+}
+
 // Macro atom (Sect. 2.5): the binary64 kernel's walk (integer thresholds, the
 // same draws in the same order) on a lane's model context; returns the
 // branching-row info of the level the atom deactivates from.
@@ -240,13 +275,15 @@ __device__ __forceinline__ void flush_stats(Stats &st, unsigned long long *dst) 
 
 // One kernel source serves a single model (p.n_models == 0) and a batch, so a
 // model's results do not depend on the company it is launched in.  It is
-// compiled twice, differing only in register allocation: MINB = 1 (up to 255
-// registers: the shortest chain for a single model's last random walks) for
-// single models, MINB = 2 (128 registers: 16 resident warps per SM instead of
-// 12) for batches, whose throughput phase dominates.  The arithmetic is the
-// same instruction for instruction; the batch tests check the bits.
+// compiled twice: MINB = 1 for single models (blocks of 128 threads, three
+// per SM at up to 168 registers, and the lone-walker mode for the last random
+// walks) and MINB = 2 for batches (128 registers: 16 resident warps per SM,
+// for the throughput phase that dominates a batch).  The arithmetic is the
+// same instruction for instruction, lone-walker mode included; the batch
+// tests check the bits.
 template <int MODE, bool JB, bool REC, int MINB>
-__global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const TransportParams p) {
+__global__ void __launch_bounds__(MINB == 1 ? 128 : kMaxBlock, MINB == 1 ? 3 : MINB)
+    transport_mixed(const TransportParams p) {
   extern __shared__ unsigned long long smem_u64[];
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lanemask_lt = (1u << lane) - 1u;
@@ -272,6 +309,23 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
   PacketM pk;
   DrawStream ds;
   bool alive = false, finished = false;
+  // Lone-walker mode (single-model build): once the packet queue is empty and
+  // a warp is down to one live walk, every lane takes that walk's state and
+  // runs its segments with the owner lane, as in the binary64 kernel: the
+  // lanes load the line list 32 lines at a time in one coalesced load (line
+  // lwin_j0 + lane in each lane), scan the window in one step, compute the
+  // walk's draws 64 at a time into a per-warp shared buffer, and only the
+  // owner lane makes the walk's side effects.
+  constexpr bool kLoneBuild = MINB == 1 && MODE != 2;
+  WarpDraws wd;
+  wd.init(batch ? nullptr : smem_u64 + 2 * static_cast<size_t>(p.S) + 2 * kWarpDraws * (threadIdx.x >> 5));
+  bool drained = false;  // warp-uniform: the packet queue is empty
+  bool lone = false;
+  int owner = 0;
+  int32_t lwin_j0 = 0, lwin_s = -1;
+  long long lwin_b = 0;
+  float lwin_t = 0.0f;
+  unsigned long long lwin_r = 0ull;
   Stats st;
 #pragma unroll
   for (int i = 0; i < kNStats; ++i) st.v[i] = 0ull;
@@ -288,14 +342,15 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
   unsigned long long lw_r0 = 0ull, lw_r1 = 0ull;
 
   for (;;) {
-    const bool need = !alive && !finished;
-    const unsigned needmask = __ballot_sync(0xffffffffu, need);
+    const bool need = !lone && !alive && !finished;
+    const unsigned needmask = lone ? 0u : __ballot_sync(0xffffffffu, need);
     if (needmask) {
       const int leader = __ffs(needmask) - 1;
       unsigned long long base = 0ull;
       if (static_cast<int>(lane) == leader)
         base = atomicAdd(p.work_counter, static_cast<unsigned long long>(__popc(needmask)));
       base = __shfl_sync(0xffffffffu, base, leader);
+      if (base + __popc(needmask) > p.n_packets) drained = true;
       if (need) {
         unsigned long long id = base + __popc(needmask & lanemask_lt);
         if (id < p.n_packets) {
@@ -353,7 +408,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
         }
       }
     }
-    if (__all_sync(0xffffffffu, finished)) break;
+    if (!lone && __all_sync(0xffffffffu, finished)) break;
     if (p.timeout_ns) {
       bool late = false;
       if (lane == 0u) late = (global_ns() - t_start) > p.timeout_ns;
@@ -372,7 +427,81 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
         break;
       }
     }
+    if (kLoneBuild && !batch) {
+      if (lone) {
+        wd.keep_u(ds, c.key0, c.key1, c.iteration, lane);
+      } else if (drained) {
+        const unsigned live = __ballot_sync(0xffffffffu, alive);
+        if (__popc(live) == 1) {
+          // the other lanes' packets are done: they hand their estimator sums
+          // over and take the walk's state
+          owner = __ffs(live) - 1;
+          if (!alive && acc_s >= 0) {
+            atomicAdd(c.est_fix + acc_s, acc_j);
+            atomicAdd(c.est_fix + c.S + acc_s, acc_nb);
+          }
+          const unsigned F = 0xffffffffu;
+          pk.nu_lab = __shfl_sync(F, pk.nu_lab, owner);
+          pk.p = __shfl_sync(F, pk.p, owner);
+          pk.q = __shfl_sync(F, pk.q, owner);
+          pk.e_lab = __shfl_sync(F, pk.e_lab, owner);
+          pk.inv_nu = __shfl_sync(F, pk.inv_nu, owner);
+          pk.inv_D = __shfl_sync(F, pk.inv_D, owner);
+          pk.shell = __shfl_sync(F, pk.shell, owner);
+          pk.next_line = __shfl_sync(F, pk.next_line, owner);
+          pk.pid = __shfl_sync(F, pk.pid, owner);
+          pk.have_inv_D = __shfl_sync(F, static_cast<int>(pk.have_inv_D), owner) != 0;
+#pragma unroll
+          for (int k = 0; k < kNCounters; ++k) pk.cnt[k] = __shfl_sync(F, pk.cnt[k], owner);
+          ds.k0 = __shfl_sync(F, ds.k0, owner);
+          ds.k1 = __shfl_sync(F, ds.k1, owner);
+          ds.packet = __shfl_sync(F, ds.packet, owner);
+          ds.iteration = __shfl_sync(F, ds.iteration, owner);
+          ds.d = __shfl_sync(F, ds.d, owner);
+          ds.spare_a = __shfl_sync(F, ds.spare_a, owner);
+          ds.spare_b = __shfl_sync(F, ds.spare_b, owner);
+          cs = __shfl_sync(F, cs, owner);
+          c_kap = __shfl_sync(F, c_kap, owner);
+          c_ikap = __shfl_sync(F, c_ikap, owner);
+          c_xi2 = __shfl_sync(F, c_xi2, owner);
+          c_xo2 = __shfl_sync(F, c_xo2, owner);
+          acc_s = __shfl_sync(F, acc_s, owner);
+          acc_j = __shfl_sync(F, acc_j, owner);
+          acc_nb = __shfl_sync(F, acc_nb, owner);
+          lwin_s = -1;
+          alive = true;
+          lone = true;
+          wd.keep_u(ds, c.key0, c.key1, c.iteration, lane);
+        }
+      }
+    }
     if (!alive) continue;
+    const bool act = !lone || static_cast<int>(lane) == owner;  // makes the walk's side effects
+    // the walk's next draw: from the warp's buffer in lone mode
+    auto next_u = [&]() -> unsigned long long { return lone ? wd.take_u53(ds) : ds.next_u53(); };
+    auto lone_reload = [&](int32_t s_, int32_t j0) {
+      lwin_j0 = j0;
+      lwin_s = s_;
+      const int32_t jj = j0 + static_cast<int32_t>(lane);
+      lwin_b = 0;
+      lwin_t = 0.0f;
+      lwin_r = 0ull;
+      if (jj < c.L) {
+        lwin_b = __ldg(reinterpret_cast<const long long *>(c.nu) + jj);
+        lwin_t = __ldg(c.tau32 + static_cast<size_t>(s_) * static_cast<size_t>(c.L) + jj);
+        if (MODE == 1) lwin_r = __ldg(c.row_info + jj);
+      }
+    };
+    auto lone_fetch = [&](int32_t s_, int32_t jj, long long &b, float &t, unsigned long long &r) {
+      int idx = jj - lwin_j0;
+      if (lwin_s != s_ || idx < 0 || idx >= 32) {
+        lone_reload(s_, jj);
+        idx = 0;
+      }
+      b = __shfl_sync(0xffffffffu, lwin_b, idx);
+      t = __shfl_sync(0xffffffffu, lwin_t, idx);
+      r = __shfl_sync(0xffffffffu, lwin_r, idx);
+    };
 
     int status = 0;
     if (pk.cnt[0] >= c.max_segments) {
@@ -396,7 +525,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
       }
       const float kap = c_kap;
       const bool thomson = kap > 0.0f;
-      const float tau0 = -__logf(open0f(ds.next_u53()));
+      const float tau0 = -__logf(open0f(next_u()));
       const float xi2 = c_xi2, xo2 = c_xo2;
       const bool inner = pp < 0.0f && q <= xi2;
       // shell exit threshold only once a line is passed or the exit wins
@@ -427,7 +556,105 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
       long long bj = 0, bj_n = 0;
       float taul = 0.0f, tau_n = 0.0f;
       unsigned long long rinfo = 0ull, rinfo_n = 0ull;
-      if (MINB == 1 && lw_ok) {
+      // An absorbing line (Sect. 2.6): with no line passed yet its Sobolev
+      // point is also placed against the shell exit; if the exit comes first
+      // the scan ends with no event (kind stays 0).
+      auto absorb = [&](long long b_, unsigned long long r_) {
+        const double nuj = __longlong_as_double(b_);
+        const float lj = f32_of_f64_max0(nu_cmf - nuj) * inv_nu;
+        if (!have_shell && !inside_shell_f(pp, q, lj, inner, xi2, xo2)) return;  // exit comes first
+        pk.cnt[2] += 1u;
+        if (JB && act)
+          red_add_evict_first(c.jb_fix + row + j, __float2ull_rn((f32_of_positive_f64(b_) * inv_nu) * e_jb), jb_pol);
+        kind = kLineEvent;
+        l = lj;
+        nu_hit = nuj;
+        rinfo_hit = r_;
+      };
+      bool fast = false;  // the lone scan settled the segment's line event
+      // downbranch: the absorbing line's emission record, loaded as soon as the
+      // lone scan names the line (the emission draw is the next in the buffer)
+      bool have_slot = false;
+      ulonglong2 slot_a = make_ulonglong2(0ull, 0ull), slot_h = make_ulonglong2(0ull, 0ull);
+      if (lone) {
+        int idx = j - lwin_j0;
+        if (lwin_s != s || idx < 0 || idx >= 32) {
+          lone_reload(s, j);
+          idx = 0;
+        }
+        if (thomson) {
+          // The scan of lines j0 + idx .. j0 + 31 of the window in one step (the
+          // binary64 kernel's window scan in this kernel's arithmetic): in the
+          // scan below the threshold after line k is T_k = thr_e + sum of the
+          // binary32 products tau_i c_e (binary64 sums); it stops at line k when
+          // nu_k <= T_{k-1} (beyond d_e), when nu_k lies beyond the shell exit
+          // (exact key comparison), or when T_k > nu_k (absorbed).  Each lane
+          // forms A = nu_k - T_{k-1} and B = nu_k - T_k in binary32 from the
+          // binary64 difference nu_k - thr_e (truncated) and a prefix sum of the
+          // same products, with a bound M on |error|: the truncation (2u) and
+          // the five summation levels (5u), the final difference (u), the scan's
+          // binary64 sums (at most 2^-48 (|thr_e| + C)) and products below the
+          // binary32 normal range that the scan drops (32 2^-126):  M = 2^-20
+          // (|d| + C) + 2^-44 |thr_e| + 2^-120.  Where every sign up to the first
+          // line that stops the scan is certain and that line absorbs, the
+          // result is the scan's; otherwise the scan below runs as usual.
+          const float pe = shell_exit_f(q, inner, xi2, xo2);
+          const long long ksh = rawkey(nu_lab * f64_of_f32(1.0f - pe));
+          const int32_t jl = lwin_j0 + static_cast<int32_t>(lane);
+          const bool cand = static_cast<int>(lane) >= idx;
+          const bool valid = cand && jl < L;
+          const float dk = f32_rz_any(__longlong_as_double(lwin_b) - thr_e);
+          float P = valid ? lwin_t * c_e : 0.0f;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(0xffffffffu, P, o);
+            if (static_cast<int>(lane) >= o) P = __fadd_rn(P, y);
+          }
+          float Px = __shfl_up_sync(0xffffffffu, P, 1);
+          if (lane == 0u) Px = 0.0f;
+          const float A = __fsub_rn(dk, Px), B = __fsub_rn(dk, P);
+          const float M = __fadd_rn(__fmul_rn(0x1.0p-20f, __fadd_rn(fabsf(dk), P)),
+                                    __fadd_rn(__fmul_rn(0x1.0p-44f, fabsf(f32_rz_any(thr_e))), 0x1.0p-120f));
+          const bool e_no = A > M;                      // certainly before d_e
+          const bool a_yes = B < -M, a_no = B > M;      // certainly absorbed / passed
+          const bool x_no = lwin_b > ksh;               // before the exit
+          const bool pass = valid && e_no && a_no && x_no;
+          const bool take = valid && e_no && a_yes && (static_cast<int>(lane) == idx || x_no);
+          const unsigned stop = __ballot_sync(0xffffffffu, cand && !pass);
+          const unsigned took = __ballot_sync(0xffffffffu, take);
+          const int kstar = __ffs(stop) - 1;
+          if (kstar >= 0 && ((took >> kstar) & 1u)) {
+            fast = true;
+            const int npass = kstar - idx;
+            pk.cnt[1] += static_cast<uint32_t>(npass + 1);
+            pk.cnt[2] += static_cast<uint32_t>(npass);
+            if (JB && cand && static_cast<int>(lane) < kstar)  // the lines passed, one lane each
+              red_add_evict_first(c.jb_fix + row + jl,
+                                  __float2ull_rn((f32_of_positive_f64(lwin_b) * inv_nu) * e_jb), jb_pol);
+            if (npass > 0) {  // as the scan leaves it after its first pass
+              p_exit = pe;
+              key_shell = ksh;
+              have_shell = true;
+            }
+            j = lwin_j0 + kstar;
+            bj = __shfl_sync(0xffffffffu, lwin_b, kstar);
+            rinfo = __shfl_sync(0xffffffffu, lwin_r, kstar);
+            if (MODE == 1) {
+              const uint32_t rb = static_cast<uint32_t>(rinfo), rlen = static_cast<uint32_t>(rinfo >> 32);
+              const uint32_t bucket = static_cast<uint32_t>(
+                  __umul64hi(wd.peek_u53(ds) << 11, static_cast<unsigned long long>(rlen)));
+              const DbrRec *slot = c.bucket + rb + bucket;
+              slot_a = __ldg(reinterpret_cast<const ulonglong2 *>(slot));
+              slot_h = __ldg(reinterpret_cast<const ulonglong2 *>(slot) + 1);
+              have_slot = true;
+            }
+          }
+        }
+        if (!fast) {
+          lone_fetch(s, j, bj, taul, rinfo);
+          lone_fetch(s, j + 1, bj_n, tau_n, rinfo_n);
+        }
+      } else if (MINB == 1 && lw_ok) {
         bj = lw_b0; taul = lw_t0; rinfo = lw_r0;
         bj_n = lw_b1; tau_n = lw_t1; rinfo_n = lw_r1;
       } else {
@@ -446,12 +673,15 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
       long long bj_nn = 0;
       float tau_nn = 0.0f;
       unsigned long long rinfo_nn = 0ull;
-      while (j < L) {
+      if (fast) absorb(bj, rinfo);
+      else while (j < L) {
         pk.cnt[1] += 1u;
         bj_nn = 0;
         tau_nn = 0.0f;
         rinfo_nn = 0ull;
-        if (j + 2 < L) {
+        if (lone) {
+          lone_fetch(s, j + 2, bj_nn, tau_nn, rinfo_nn);
+        } else if (j + 2 < L) {
           bj_nn = __ldg(nub + j + 2);
           tau_nn = __ldg(tau_s + j + 2);
           if (MODE == 1) rinfo_nn = __ldg(c.row_info + j + 2);
@@ -475,7 +705,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
             if (bj <= key_shell) break;  // this line lies beyond the exit
           }
           pk.cnt[2] += 1u;
-          if (JB) red_add_evict_first(c.jb_fix + row + j, __float2ull_rn((f32_of_positive_f64(bj) * inv_nu) * e_jb), jb_pol);
+          if (JB && act) red_add_evict_first(c.jb_fix + row + j, __float2ull_rn((f32_of_positive_f64(bj) * inv_nu) * e_jb), jb_pol);
           if (thomson) {
             thr_e = t;
             key_e = rawkey(t);
@@ -484,14 +714,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
             tau_rem -= taul;
           }
         } else {
-          const float lj = f32_of_f64_max0(nu_cmf - nuj) * inv_nu;
-          if (!have_shell && !inside_shell_f(pp, q, lj, inner, xi2, xo2)) break;  // exit comes first
-          pk.cnt[2] += 1u;
-          if (JB) red_add_evict_first(c.jb_fix + row + j, __float2ull_rn((f32_of_positive_f64(bj) * inv_nu) * e_jb), jb_pol);
-          kind = kLineEvent;
-          l = lj;
-          nu_hit = nuj;
-          rinfo_hit = rinfo;
+          absorb(bj, rinfo);
           break;
         }
         ++j;
@@ -514,7 +737,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
       // estimators: binary32 contribution (units of E), summed in fixed point
       const float wgt = eD2 * l;
       if (s != acc_s) {
-        if (acc_s >= 0) {
+        if (acc_s >= 0 && act) {
           atomicAdd(c.est_fix + acc_s, acc_j);
           atomicAdd(c.est_fix + c.S + acc_s, acc_nb);
         }
@@ -549,9 +772,13 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
             const unsigned long long rinfo_em =
                 MODE == 2 ? macroatom_walk_m(c, __ldg(c.line_row + j), ds) : rinfo_hit;
             int32_t emit;
-            pick_m(c, rinfo_em, ds.next_u53(), nu_c, inv_nu_c, emit);
+            const unsigned long long u_em = next_u();
+            if (have_slot) pick_lone_m(c, rinfo_em, u_em, slot_a, slot_h, lane, nu_c, inv_nu_c, emit);
+            else pick_m(c, rinfo_em, u_em, nu_c, inv_nu_c, emit);
             pk.next_line = emit + 1;
-            if (MINB == 1) {  // the next segment's first lines, loaded now
+            if (lone) {
+              lone_reload(s, pk.next_line);
+            } else if (MINB == 1) {  // the next segment's first lines, loaded now
               const int32_t nl = pk.next_line;
               lw_b0 = 0; lw_t0 = 0.0f; lw_r0 = 0ull; lw_b1 = 0; lw_t1 = 0.0f; lw_r1 = 0ull;
               if (nl < L) {
@@ -586,7 +813,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
             lw_ok = true;
           }
         }
-        const unsigned long long um = ds.next_u53();
+        const unsigned long long um = next_u();
         const float mu2 = static_cast<float>(static_cast<long long>(um >> 29) - (1ll << 23)) * 0x1.0p-23f;
         const float pn = xn * mu2;
         const float D2 = 1.0f - pn;
@@ -603,7 +830,14 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
         pk.have_inv_D = true;
       }
     }
-    if (status != 0) {
+    if (status != 0 && !act) {  // lone mode, not the owner lane: drop the adopted walk
+      alive = false;
+      lone = false;
+      acc_s = -1;
+      acc_j = 0ull;
+      acc_nb = 0ull;
+    } else if (status != 0) {
+      lone = false;
       if (status == 1) st.v[kStEscaped] += 1ull;
       else if (status == 2) st.v[kStReabsorbed] += 1ull;
       else st.v[kStCapped] += 1ull;
@@ -636,7 +870,7 @@ __global__ void __launch_bounds__(kMaxBlock, MINB) transport_mixed(const Transpo
     }
   }
   if (cur_model >= 0) {
-    if (acc_s >= 0) {
+    if (acc_s >= 0 && (!lone || static_cast<int>(lane) == owner)) {  // (a launch stopped in lone mode)
       atomicAdd(c.est_fix + acc_s, acc_j);
       atomicAdd(c.est_fix + c.S + acc_s, acc_nb);
     }
@@ -670,7 +904,11 @@ const void *select_b(int line_mode, bool jb, bool rec) { return select_m<2>(line
 
 const void *select_mixed_kernel(int line_mode, bool jb, bool rec) { return select_m<1>(line_mode, jb, rec); }
 
-size_t mixed_smem_bytes(int S) { return 4 * static_cast<size_t>(S) * sizeof(float); }
+// single-model launches (128 threads): shell tables, then a lone walker's
+// draw buffer per warp
+size_t mixed_smem_bytes(int S) {
+  return 4 * static_cast<size_t>(S) * sizeof(float) + (128 / 32) * 2 * kWarpDraws * sizeof(unsigned long long);
+}
 
 cudaError_t batch_occupancy(int line_mode, bool j_blue, bool record, int n_models, int block,
                             int *blocks_per_sm) {
