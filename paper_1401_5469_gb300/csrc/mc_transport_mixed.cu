@@ -256,9 +256,9 @@ __device__ __forceinline__ bool inside_shell_f(float pp, float q, float l, bool 
   return inner ? (pl < 0.0f && r2 > xi2) : r2 < xo2;
 }
 
-// uniform in (0, 1] with 24 random bits
+// uniform in (0, 1] with 24 random bits (a 32-bit conversion)
 __device__ __forceinline__ float open0f(unsigned long long u53) {
-  return static_cast<float>((u53 >> 29) + 1ull) * 0x1.0p-24f;
+  return static_cast<float>(static_cast<uint32_t>(u53 >> 29) + 1u) * 0x1.0p-24f;
 }
 
 struct Stats {
@@ -814,7 +814,7 @@ __global__ void __launch_bounds__(MINB == 1 ? 128 : kMaxBlock, MINB == 1 ? 3 : M
           }
         }
         const unsigned long long um = next_u();
-        const float mu2 = static_cast<float>(static_cast<long long>(um >> 29) - (1ll << 23)) * 0x1.0p-23f;
+        const float mu2 = static_cast<float>(static_cast<int32_t>(um >> 29) - (1 << 23)) * 0x1.0p-23f;
         const float pn = xn * mu2;
         const float D2 = 1.0f - pn;
         const float iD2 = 1.0f / D2;
