@@ -70,10 +70,10 @@ L2_BYTES = 129 * 2**20
 # kernel built from these sources only: with any other source hash the
 # bench reports traffic as null.
 TRAFFIC_CAPTURE = {
-    "dram_bytes_per_launch": 777.38e6 + 131.70e6,
+    "dram_bytes_per_launch": 926.16e6 + 159.46e6,
     "sources": ("paper_1401_5469_gb300/csrc/mc_transport.cu", "paper_1401_5469_gb300/csrc/mc_device.cuh",
                 "paper_1401_5469_gb300/csrc/mc_internal.h"),
-    "sha256": "43e90e509671a99020bd51672412f7f6ed712dce0fcfe7b9265fadcd3309d923",
+    "sha256": "ae378750c28e5acbd762a61c9dc7d0c56a9a69b5d83c1c9c54d9d130027e2355",
 }
 
 
@@ -83,7 +83,7 @@ TRAFFIC_CAPTURE = {
 # for other sources.  (Lane operations would count the redundant lanes of the
 # lone-walker mode, where the whole warp runs one walk.)
 FP64_OPS_CAPTURE = {
-    "warp_instructions_per_segment": 9.356,
+    "warp_instructions_per_segment": 8.950,
     "sources": TRAFFIC_CAPTURE["sources"],
     "sha256": TRAFFIC_CAPTURE["sha256"],
 }
