@@ -394,6 +394,10 @@ mc_status mc_batch_run_iteration(mc_batch *b, const uint64_t *seeds, const uint3
 mc_status mc_batch_synchronize(mc_batch *b);
 /* Device time of the last batched transport launch, ms[0] (synchronises). */
 mc_status mc_batch_read_timing(mc_batch *b, float *ms);
+/* Phases of the last batched transport launch, as mc_read_transport_phases:
+ * ms[0] until the packet queue of all models ran empty, ms[1] from then until
+ * the last warp finished (synchronises). */
+mc_status mc_batch_read_phases(mc_batch *b, float *ms);
 const char *mc_batch_last_error_message(const mc_batch *b);
 void mc_batch_destroy(mc_batch *b);
 

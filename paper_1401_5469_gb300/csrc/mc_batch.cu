@@ -308,6 +308,19 @@ mc_status mc_batch_read_timing(mc_batch *b, float *ms) {
   return MC_OK;
 }
 
+mc_status mc_batch_read_phases(mc_batch *b, float *ms) {
+  if (!b || !ms) return MC_ERR_INVALID_ARG;
+  if (!b->iterations) return bfail(b, MC_ERR_NOT_READY, "no batched iteration yet");
+  unsigned long long f[3];  // flags [1] queue empty, [2] last warp done, [3] first warp start (ns)
+  cudaError_t e = cudaMemcpyAsync(f, b->d_counters + 2, sizeof(f), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(b, e, "batch phases");
+  const unsigned long long empty = f[0], done = f[1], start = f[2];
+  ms[0] = (empty > start) ? static_cast<float>((empty - start) * 1e-6) : 0.0f;
+  ms[1] = (done > empty && empty) ? static_cast<float>((done - empty) * 1e-6) : 0.0f;
+  return MC_OK;
+}
+
 const char *mc_batch_last_error_message(const mc_batch *b) { return b ? b->err.c_str() : ""; }
 
 mc_status mc_batch_set_launch(mc_batch *b, const mc_batch_launch *launch) {

@@ -43,7 +43,7 @@ EXPORTED = ("mc_model_create", "mc_set_plasma", "mc_run_iteration", "mc_run_iter
             "mc_read_timing", "mc_read_transport_phases", "mc_launch_count", "mc_synchronize", "mc_model_destroy",
             "mc_status_string", "mc_last_error_message", "mc_transport_noalloc",
             "mc_batch_create", "mc_batch_run_iteration", "mc_batch_synchronize",
-            "mc_batch_read_timing", "mc_batch_last_error_message", "mc_batch_destroy",
+            "mc_batch_read_timing", "mc_batch_read_phases", "mc_batch_last_error_message", "mc_batch_destroy",
             "mc_batch_set_launch", "mc_batch_get_launch", "mc_batch_autotune", "mc_batch_capture_graph",
             "mc_device_estimators", "mc_set_virtual_packets", "mc_read_virtual_spectrum",
             "mc_t_inner_from_luminosity", "mc_emitted_luminosity", "mc_t_inner_update",
@@ -203,6 +203,8 @@ def load(build_if_missing: bool = True):
     L.mc_batch_synchronize.argtypes = [vp]
     L.mc_batch_read_timing.restype = i32
     L.mc_batch_read_timing.argtypes = [vp, vp]
+    L.mc_batch_read_phases.restype = i32
+    L.mc_batch_read_phases.argtypes = [vp, vp]
     L.mc_batch_last_error_message.restype = C.c_char_p
     L.mc_batch_last_error_message.argtypes = [vp]
     L.mc_batch_destroy.restype = None
@@ -661,6 +663,12 @@ class Batch:
         ms = np.zeros(1, dtype=np.float32)
         self._bcheck(load().mc_batch_read_timing(self.h, _p(ms)))
         return float(ms[0])
+
+    def phases(self):
+        """mc_batch_read_phases: (ms until the packet queue ran empty, ms of the tail)."""
+        ms = np.zeros(2, dtype=np.float32)
+        self._bcheck(load().mc_batch_read_phases(self.h, _p(ms)))
+        return float(ms[0]), float(ms[1])
 
     def close(self):
         if getattr(self, "h", None):

@@ -82,11 +82,13 @@ def run_batched(a):
     for it in range(a.iterations):
         b.run_iteration(seeds, it, n, t, update=bool(a.update))
         ms = b.transport_ms()
+        phases = b.phases()
         tot = {}
         for m in models:
             for k, v in m.spectrum()[1].items():
                 tot[k] = tot.get(k, 0) + v
-        print(json.dumps({"iteration": it, "models": len(specs), "transport_ms": ms, **tot}), flush=True)
+        print(json.dumps({"iteration": it, "models": len(specs), "transport_ms": ms, "queue_ms": phases[0],
+                          "tail_ms": phases[1], **tot}), flush=True)
     b.close()
     for m in models:
         m.close()

@@ -83,6 +83,9 @@ def test_batch_equals_solo(mc):
             t, w, _ = m.plasma()
             assert np.array_equal(t, t_s) and np.array_equal(w, w_s), (k, it)
     assert b.transport_ms() > 0
+    queue_ms, tail_ms = b.phases()  # global-timer phases of the same launch
+    assert queue_ms > 0 and tail_ms >= 0
+    assert queue_ms + tail_ms <= 1.05 * b.transport_ms() + 0.05
     b.close()
     for m in models:
         m.close()
