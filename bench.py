@@ -73,7 +73,7 @@ TRAFFIC_CAPTURE = {
     "dram_bytes_per_launch": 926.16e6 + 159.46e6,
     "sources": ("paper_1401_5469_gb300/csrc/mc_transport.cu", "paper_1401_5469_gb300/csrc/mc_device.cuh",
                 "paper_1401_5469_gb300/csrc/mc_internal.h"),
-    "sha256": "ae378750c28e5acbd762a61c9dc7d0c56a9a69b5d83c1c9c54d9d130027e2355",
+    "sha256": "e4c4c379fed63669b54937f5e16c6ad4aec6471b33587f832d0557eff18b1f92",
 }
 
 

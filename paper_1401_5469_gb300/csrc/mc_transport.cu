@@ -20,13 +20,20 @@
 //    test tau_S + kappa d_line > tau with kappa d = (nu_cmf - nu) / (nu_lab/k));
 //    every comparison is an integer compare of the values' bit patterns
 //    (one operand is always positive, so the patterns order like the values);
-//  * 1/D and 1/nu_lab are carried and refreshed with Newton reciprocals, and
+//  * 1/D and 1/nu_lab are carried and refreshed with Newton reciprocals,
+//    E/nu_lab is carried instead of E_lab (the same in both frames), and
 //    -ln z comes from a table-driven logarithm;
 //  * downbranch emission is an integer guide-table search, and the next
 //    line's nu/tau loads are issued before the current line is resolved;
 //  * lanes stay converged: a lane that finishes claims the next packet at the
 //    loop head (warp-aggregated atomic); shell estimators accumulate in
-//    registers and are flushed once per shell change.
+//    registers and are flushed once per shell change;
+//  * a warp down to its last live walk runs it with all 32 lanes (lone-walker
+//    mode): the line list 32 lines at a time, the scan of such a window in
+//    one step through a binary32 filter with an error bound (the scalar scan
+//    wherever a sign is within the bound), the absorbing line's emission
+//    record loaded as soon as the scan names it, and the walk's draws
+//    computed ahead by the whole warp.
 #include <cstdint>
 
 #include "mc_device.cuh"

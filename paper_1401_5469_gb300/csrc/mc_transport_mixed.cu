@@ -21,6 +21,12 @@
 // longest random walks start first); a lane that claims a packet of another
 // model loads that model's context and first flushes its register
 // accumulators to the previous model.
+//
+// Single-model launches also have the binary64 kernel's lone-walker mode: a
+// warp down to its last live walk runs it with all 32 lanes (32-line windows
+// scanned in one step through a binary32 filter against this kernel's own
+// threshold chain, the emission record loaded as soon as the scan names the
+// line, the walk's draws computed ahead by the warp).
 #include <cstdint>
 
 #include "mc_device.cuh"
