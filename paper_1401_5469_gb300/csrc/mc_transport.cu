@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(kBlock) transport_fp64(const TransportParams p
       wd.keep(ds, p.key0, p.key1, p.iteration, lane);
     } else {
       wd.prepare(alive, __any_sync(0xffffffffu, finished), ds, pk.pid, p.key0, p.key1, p.iteration, lane);
-      if (wd.on && MODE != 2 && !p.n_virtual) {
+      if (wd.on && !p.n_virtual) {
         // enter lone-walker mode: the other lanes' packets are done; they hand
         // their estimator sums over and take the walk's state
         owner = __ffs(__ballot_sync(0xffffffffu, alive)) - 1;
