@@ -73,7 +73,7 @@ TRAFFIC_CAPTURE = {
     "dram_bytes_per_launch": 926.16e6 + 159.46e6,
     "sources": ("paper_1401_5469_gb300/csrc/mc_transport.cu", "paper_1401_5469_gb300/csrc/mc_device.cuh",
                 "paper_1401_5469_gb300/csrc/mc_internal.h"),
-    "sha256": "e4c4c379fed63669b54937f5e16c6ad4aec6471b33587f832d0557eff18b1f92",
+    "sha256": "309bc2792b36959d9057086d024a7347dd831c4869688afaae1a866dbc6c0124",
 }
 
 
