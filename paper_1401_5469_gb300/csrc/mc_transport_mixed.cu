@@ -223,17 +223,27 @@ __device__ __forceinline__ void pick_lone_m(const MCtx &c, unsigned long long ri
 // Macro atom (Sect. 2.5): the binary64 kernel's walk (integer thresholds, the
 // same draws in the same order) on a lane's model context; returns the
 // branching-row info of the level the atom deactivates from.
-__device__ __forceinline__ unsigned long long macroatom_walk_m(const MCtx &c, int32_t row, DrawStream &ds) {
+// In lone-walker mode (wd non-null) the draws come from the warp's buffer,
+// and past its end each is computed on its own: the same values either way.
+__device__ __forceinline__ unsigned long long ma_draw(DrawStream &ds, const WarpDraws *wd) {
+  if (!wd) return ds.next_u53();
+  if (ds.d - wd->base < kWarpDraws) return wd->take_u53(ds);
+  ++ds.d;
+  return u53_past_buffer(ds.k0, ds.k1, ds.packet, ds.iteration, ds.d - 1u);
+}
+
+__device__ __forceinline__ unsigned long long macroatom_walk_m(const MCtx &c, int32_t row, DrawStream &ds,
+                                                               const WarpDraws *wd) {
   for (uint32_t n = 0; n < kMaMaxJumps; ++n) {
     const MaRow *mr = c.ma_row + row;
     const unsigned long long thr = __ldg(&mr->jump_thr);
     const uint2 jb = __ldg(reinterpret_cast<const uint2 *>(&mr->jump_begin));  // begin, length
-    const unsigned long long za = ds.next_u53();
+    const unsigned long long za = ma_draw(ds, wd);
     if (!(za < thr)) {
       const uint2 db = __ldg(reinterpret_cast<const uint2 *>(&mr->dbr_begin));
       return static_cast<unsigned long long>(db.x) | (static_cast<unsigned long long>(db.y) << 32);
     }
-    const unsigned long long zb = ds.next_u53();
+    const unsigned long long zb = ma_draw(ds, wd);
     const MaJump *jp = c.ma_jump + jb.x;
     int32_t next = __ldg(&jp[jb.y - 1].target);
     for (uint32_t k = 0; k < jb.y; ++k) {
@@ -322,7 +332,7 @@ __global__ void __launch_bounds__(MINB == 1 ? 128 : kMaxBlock, MINB == 1 ? 3 : M
   // lwin_j0 + lane in each lane), scan the window in one step, compute the
   // walk's draws 64 at a time into a per-warp shared buffer, and only the
   // owner lane makes the walk's side effects.
-  constexpr bool kLoneBuild = MINB == 1 && MODE != 2;
+  constexpr bool kLoneBuild = MINB == 1;
   WarpDraws wd;
   wd.init(batch ? nullptr : smem_u64 + 2 * static_cast<size_t>(p.S) + 2 * kWarpDraws * (threadIdx.x >> 5));
   bool drained = false;  // warp-uniform: the packet queue is empty
@@ -484,7 +494,11 @@ __global__ void __launch_bounds__(MINB == 1 ? 128 : kMaxBlock, MINB == 1 ? 3 : M
     if (!alive) continue;
     const bool act = !lone || static_cast<int>(lane) == owner;  // makes the walk's side effects
     // the walk's next draw: from the warp's buffer in lone mode
-    auto next_u = [&]() -> unsigned long long { return lone ? wd.take_u53(ds) : ds.next_u53(); };
+    // (a macro atom's internal jumps can take more draws than the buffer holds)
+    auto next_u = [&]() -> unsigned long long {
+      if (!lone) return ds.next_u53();
+      return MODE == 2 ? ma_draw(ds, &wd) : wd.take_u53(ds);
+    };
     auto lone_reload = [&](int32_t s_, int32_t j0) {
       lwin_j0 = j0;
       lwin_s = s_;
@@ -776,7 +790,7 @@ __global__ void __launch_bounds__(MINB == 1 ? 128 : kMaxBlock, MINB == 1 ? 3 : M
           if (MODE >= 1) {
             // MODE 2: macro atom, internal jumps before the emission pick
             const unsigned long long rinfo_em =
-                MODE == 2 ? macroatom_walk_m(c, __ldg(c.line_row + j), ds) : rinfo_hit;
+                MODE == 2 ? macroatom_walk_m(c, __ldg(c.line_row + j), ds, lone ? &wd : nullptr) : rinfo_hit;
             int32_t emit;
             const unsigned long long u_em = next_u();
             if (have_slot) pick_lone_m(c, rinfo_em, u_em, slot_a, slot_h, lane, nu_c, inv_nu_c, emit);

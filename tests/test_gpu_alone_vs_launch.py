@@ -7,8 +7,8 @@ packet run alone (mc_run_iteration_range with one packet: its warp is in that
 state from its first segment) must therefore reproduce, bit for bit, the
 status, final frequency, energy and counters it has in a full launch (where it
 mostly shares its warp).  The twelve longest walks of a 2e4-packet downbranch
-iteration are checked, in binary64 and in mixed precision, and in binary64
-with macro-atom line interactions.
+iteration are checked, in binary64 and in mixed precision, with downbranch
+and with macro-atom line interactions.
 """
 import numpy as np
 import pytest
@@ -28,7 +28,7 @@ def mc():
     return mcmod
 
 
-@pytest.mark.parametrize("precision,line_mode", [(0, 1), (1, 1), (0, 2)])
+@pytest.mark.parametrize("precision,line_mode", [(0, 1), (1, 1), (0, 2), (1, 2)])
 def test_packets_alone_equal_their_full_launch_records(mc, precision, line_mode):
     make = synth.downbranch_model if line_mode == 1 else synth.macroatom_model
     spec = make(n_lines=40000, n_shells=16, n_packets=20000, seed=4242)
